@@ -1,0 +1,130 @@
+"""Seeded synthetic inputs: lattices, couplings and symmetry groups.
+
+This module holds no arithmetic of the method.  It only produces the inputs
+that both the CUDA path and the CPU oracle receive: bond lists, coupling
+values drawn from a seed, site permutations of translation groups and the
+characters of their one-dimensional irreps.
+
+Site labelling: a rectangular Lx x Ly lattice numbers site (x, y) as
+i = x + Lx*y, periodic in both directions.  Bit i of a state word is site i.
+"""
+from __future__ import annotations
+
+import cmath
+import math
+
+import numpy as np
+
+
+def _dedupe(pairs):
+    seen, out = set(), []
+    for i, j in pairs:
+        if i == j:
+            continue
+        key = (min(i, j), max(i, j))
+        if key in seen:
+            continue
+        seen.add(key)
+        out.append((i, j))
+    return out
+
+
+def chain(N: int) -> np.ndarray:
+    """Periodic chain bonds (i, i+1 mod N) (Sec. 3.2 and its TOML listing in
+    Sec. 3.8); for N = 2 the two periodic bonds are the same pair, kept once."""
+    return np.array(_dedupe([(i, (i + 1) % N) for i in range(N)]), dtype=np.int32)
+
+
+def ladder(L: int, rung_copies: int = 2) -> np.ndarray:
+    """Two-leg periodic ladder on the L x 2 lattice (leg y=0 is sites 0..L-1,
+    leg y=1 is sites L..2L-1).  Bond order: leg 0 (i, i+1), leg 1, then the
+    rungs (i, i+L) once per copy.  rung_copies=2 is what a periodic L x 2
+    square-lattice generator produces (each rung listed twice, 4L bonds, 56
+    for L=14); rung_copies=1 gives the 3L-bond ladder."""
+    b = [(i, (i + 1) % L) for i in range(L)]
+    b += [(L + i, L + (i + 1) % L) for i in range(L)]
+    for _ in range(rung_copies):
+        b += [(i, i + L) for i in range(L)]
+    return np.array(b, dtype=np.int32)
+
+
+def square_j1j2(Lx: int, Ly: int, J1: float = 1.0, J2: float = 0.5):
+    """Periodic Lx x Ly square lattice: J1 on (x+1, y) and (x, y+1), J2 on
+    (x+1, y+1) and (x-1, y+1).  Each unordered pair kept once.  Returns
+    (bonds [nb, 2] int32, J [nb] float64), J1 bonds first."""
+    s = lambda x, y: (x % Lx) + Lx * (y % Ly)  # noqa: E731
+    nn = _dedupe([(s(x, y), s(x + 1, y)) for y in range(Ly) for x in range(Lx)]
+                 + [(s(x, y), s(x, y + 1)) for y in range(Ly) for x in range(Lx)])
+    nnn = _dedupe([(s(x, y), s(x + 1, y + 1)) for y in range(Ly) for x in range(Lx)]
+                  + [(s(x, y), s(x - 1, y + 1)) for y in range(Ly) for x in range(Lx)])
+    nnn = [p for p in nnn if (min(p), max(p)) not in {(min(q), max(q)) for q in nn}]
+    bonds = np.array(nn + nnn, dtype=np.int32)
+    J = np.array([J1] * len(nn) + [J2] * len(nnn), dtype=np.float64)
+    return bonds, J
+
+
+def uniform_couplings(nb: int, seed: int, lo: float = 0.5, hi: float = 1.5) -> np.ndarray:
+    """J_b ~ U[lo, hi) from numpy's PCG64 stream seeded with `seed`."""
+    return np.random.default_rng(seed).uniform(lo, hi, size=nb).astype(np.float64)
+
+
+def random_bonds(N: int, nb: int, seed: int) -> np.ndarray:
+    """nb distinct random site pairs (for parity tests on irregular graphs)."""
+    rng = np.random.default_rng(seed)
+    pairs = set()
+    out = []
+    while len(out) < nb:
+        i, j = (int(v) for v in rng.integers(0, N, size=2))
+        if i == j or (min(i, j), max(i, j)) in pairs:
+            continue
+        pairs.add((min(i, j), max(i, j)))
+        out.append((i, j))
+    return np.array(out, dtype=np.int32)
+
+
+# ------------------------------------------------------------- symmetry
+def chain_translations(N: int) -> np.ndarray:
+    """perms[n][i] = (i + n) mod N, the powers T^n of the chain translation."""
+    return np.array([[(i + n) % N for i in range(N)] for n in range(N)], dtype=np.int32)
+
+
+def torus_translations(Lx: int, Ly: int) -> np.ndarray:
+    """perms[a + Lx*b][i] = site of (x+a, y+b) for i = (x, y)."""
+    out = []
+    for b in range(Ly):
+        for a in range(Lx):
+            out.append([((i % Lx + a) % Lx) + Lx * ((i // Lx + b) % Ly) for i in range(Lx * Ly)])
+    return np.array(out, dtype=np.int32)
+
+
+def chain_characters(N: int, m: int) -> np.ndarray:
+    """chi_k(T^n) = exp(i k n) with k = 2 pi m / N (Sec. 3.9.2)."""
+    k = 2 * math.pi * m / N
+    return np.array([cmath.exp(1j * k * n) for n in range(N)], dtype=np.complex128)
+
+
+def torus_characters(Lx: int, Ly: int, mx: int, my: int) -> np.ndarray:
+    """chi(T_x^a T_y^b) = exp(i (kx a + ky b)), kx = 2 pi mx / Lx, ky = 2 pi my / Ly."""
+    kx, ky = 2 * math.pi * mx / Lx, 2 * math.pi * my / Ly
+    out = []
+    for b in range(Ly):
+        for a in range(Lx):
+            z = cmath.exp(1j * (kx * a + ky * b))
+            out.append(complex(round(z.real, 15), round(z.imag, 15)))
+    return np.array(out, dtype=np.complex128)
+
+
+# ------------------------------------------------------------- workloads
+def batched_instances(count: int = 64, seed: int = 4, sizes=(18, 20, 22, 24, 26, 28)):
+    """Uneven batch of Heisenberg instances: N uniform over `sizes`, type
+    uniform over {chain, ladder (N/2 rungs, each rung twice)}, couplings
+    U[0.5, 1.5).  Returns a list of dicts with N, nup=N/2, kind, bonds, J."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        N = int(rng.choice(sizes))
+        kind = "chain" if rng.integers(0, 2) == 0 else "ladder"
+        bonds = chain(N) if kind == "chain" else ladder(N // 2, 2)
+        J = rng.uniform(0.5, 1.5, size=bonds.shape[0]).astype(np.float64)
+        out.append(dict(N=N, nup=N // 2, kind=kind, bonds=bonds, J=J))
+    return out

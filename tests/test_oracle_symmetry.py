@@ -1,0 +1,127 @@
+"""Pins of the oracle's symmetry-adapted blocks (Sec. 3.9, Sec. 3.10)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2505_02901_gb300 import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _toml_group():
+    perms, chis = [], {}
+    for line in open(os.path.join(GOLD, "sym_c4_toml.txt")):
+        t = line.split()
+        if not t or t[0].startswith("#"):
+            continue
+        if t[0] == "perm":
+            perms.append([int(v) for v in t[1:]])
+        else:
+            v = [float(a) for a in t[1:]]
+            chis[t[0]] = np.array([complex(v[2 * i], v[2 * i + 1]) for i in range(len(v) // 2)])
+    return np.array(perms, dtype=np.int32), chis
+
+
+def test_paper_worked_example(orc):
+    perms, chis = _toml_group()
+    st = orc.enumerate_states(4, 2)
+    v = orc.project(4, perms, chis["pi"], 0b1100, st)
+    ref = {}
+    for line in open(os.path.join(GOLD, "sym_c4_kpi.txt")):
+        t = line.split()
+        if t and not t[0].startswith("#"):
+            ref[int(t[0])] = float(t[1])
+    expect = np.zeros(st.size, dtype=np.complex128)
+    for w, c in ref.items():
+        expect[orc.index_search(st, w)] = c
+    assert np.abs(v - expect).max() < 1e-15
+
+
+def test_toml_representations_are_valid(orc):
+    perms, chis = _toml_group()
+    assert orc.group_check(4, perms) == 0
+    for name in ("zero", "pihalf", "pi"):
+        assert orc.group_check(4, perms, chis[name]) == 0
+
+
+def test_group_axiom_failures(orc):
+    perms, chis = _toml_group()
+    assert orc.group_check(4, perms[1:]) == 2                 # no identity
+    assert orc.group_check(4, perms[[0, 1]]) == 3             # not closed
+    bad = perms.copy(); bad[1] = [0, 0, 1, 2]
+    assert orc.group_check(4, bad) == 1                       # not a permutation
+    chi = chis["pihalf"].copy(); chi[2] = 1.0
+    assert orc.group_check(4, perms, chi) == 5                # not a homomorphism
+    assert orc.group_check(4, perms, 2 * chis["zero"]) in (5, 6)
+
+
+CASES = [("chain", 8, None), ("chain", 10, None), ("torus", 2, 4), ("torus", 3, 3)]
+
+
+def _case(kind, a, b):
+    if kind == "chain":
+        return a, W.chain(a), np.ones(a), W.chain_translations(a), \
+            [W.chain_characters(a, m) for m in range(a)]
+    bonds, J = W.square_j1j2(a, b, 1.0, 0.5)
+    return a * b, bonds, J, W.torus_translations(a, b), \
+        [W.torus_characters(a, b, mx, my) for my in range(b) for mx in range(a)]
+
+
+@pytest.mark.parametrize("kind,a,b", CASES)
+def test_dims_burnside_and_sum(orc, kind, a, b):
+    N, bonds, J, perms, chis = _case(kind, a, b)
+    for nup in range(N + 1):
+        dims = []
+        for chi in chis:
+            blk = orc.SymBlock(N, nup, perms, chi)
+            assert blk.dim == orc.burnside_dim(N, nup, perms, chi)
+            assert np.all(np.diff(blk.reps.astype(np.int64)) > 0)
+            dims.append(blk.dim)
+        assert sum(dims) == math.comb(N, nup)
+
+
+@pytest.mark.parametrize("kind,a,b", CASES)
+def test_symmetric_matrix_equals_projection(orc, kind, a, b):
+    N, bonds, J, perms, chis = _case(kind, a, b)
+    nup = N // 2
+    st = orc.enumerate_states(N, nup)
+    H = orc.dense_u1(N, st, bonds, J)
+    spec = []
+    for chi in chis:
+        blk = orc.SymBlock(N, nup, perms, chi)
+        if blk.dim == 0:
+            continue
+        B = blk.lift(st)
+        assert np.abs(B.conj().T @ B - np.eye(blk.dim)).max() < 1e-13
+        Hk = blk.dense(bonds, J)
+        assert np.abs(Hk - B.conj().T @ H @ B).max() < 1e-13
+        assert np.abs(Hk - Hk.conj().T).max() < 1e-14
+        spec.append(np.linalg.eigvalsh(Hk))
+    # union of the momentum spectra is the U(1) spectrum
+    assert np.abs(np.sort(np.concatenate(spec)) - np.linalg.eigvalsh(H)).max() < 1e-11
+
+
+def test_lifted_eigenvector_has_its_momentum(orc):
+    N = 10
+    bonds, perms = W.chain(N), W.chain_translations(N)
+    st = orc.enumerate_states(N, 5)
+    T = np.zeros((st.size, st.size))
+    for k, s in enumerate(st):
+        T[orc.index_search(st, orc.act(N, perms[1], int(s))), k] = 1.0
+    for m in (0, 1, 3):
+        chi = W.chain_characters(N, m)
+        blk = orc.SymBlock(N, 5, perms, chi)
+        w, V = np.linalg.eigh(blk.dense(bonds, np.ones(N)))
+        psi = blk.lift(st) @ V[:, 0]
+        assert np.abs(T @ psi - chi[1] * psi).max() < 1e-12
+
+
+def test_burnside_6x6_momentum_sectors(orc):
+    perms = W.torus_translations(6, 6)
+    assert orc.burnside_dim(36, 18, perms, W.torus_characters(6, 6, 0, 0)) == 252091362
+    assert orc.burnside_dim(36, 18, perms, W.torus_characters(6, 6, 1, 0)) == 252085716
+    total = sum(orc.burnside_dim(36, 18, perms, W.torus_characters(6, 6, mx, my))
+                for mx in range(6) for my in range(6))
+    assert total == math.comb(36, 18)
