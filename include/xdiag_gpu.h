@@ -1,0 +1,195 @@
+/*
+ * xdiag_gpu.h -- C ABI of the GB300 matrix-free spin-1/2 Heisenberg library.
+ *
+ * The operation is the product y = H x of XDiag's Lanczos iteration
+ * (Sec. 3.5 "apply", Sec. 5.1 apply_terms), for
+ *     H = sum_b J_b S_{i_b} . S_{j_b}                      (Eq. 1, App. A SdotS)
+ * on a block of fixed magnetisation (Spinhalf(N, nup), Sec. 3.1) or on a
+ * symmetry-adapted block of a 1-D representation of a site-permutation group
+ * (Spinhalf(N, nup, irrep), Sec. 3.9-3.10).  Around it: the Lanczos
+ * eigensolver (eigval0 / eigvals_lanczos / eig0, Sec. 3.6.1), per-bond
+ * expectation values (inner, Sec. 3.7) used as dE0/dJ_b, and a batched
+ * product over many independent blocks (the multi-vector apply of Sec. 5.1).
+ *
+ * Conventions
+ *   - Bit i of a state word is site i; a set bit is an up spin.  The U(1)
+ *     block lists every N-bit word with nup set bits in ascending order with
+ *     0-based indices (Sec. 3.1).  A symmetric block lists the
+ *     representatives (the smallest integer of each orbit, Sec. 3.10) whose
+ *     projected state does not vanish, ascending.
+ *   - A permutation g acts by (g s)_i = s_{g(i)}; the basis state of the
+ *     representative r is (1/N_r) sum_g conj(chi(g)) g|r>,
+ *     N_r = sqrt(|G| |Stab(r)|) (Sec. 3.10).
+ *   - Vectors are device arrays in the caller's memory, row-major
+ *     [dim][nvec]; complex vectors interleave (re, im) doubles.
+ *
+ * Ownership and errors
+ *   - The caller owns every vector it passes (x, y, g, psi0).  The library
+ *     owns its index tables and workspaces; *_destroy frees them.
+ *   - Every call returns an xd_status; nothing throws across the ABI.  On an
+ *     error the thread-local message of xd_last_error() says why.  Inputs
+ *     are validated before anything is launched.
+ *   - Calls that take a cudaStream_t are asynchronous on that stream (NULL
+ *     is the legacy default stream); calls that return host scalars
+ *     synchronise.
+ *   - A handle may be used from one host thread at a time.
+ */
+#ifndef XDIAG_GPU_H
+#define XDIAG_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *xd_stream; /* same type as cudaStream_t */
+
+typedef enum {
+    XD_OK = 0,
+    XD_EINVAL = 1,   /* bad argument (N, nup, bonds, dtype, null pointer, ...) */
+    XD_ERANGE = 2,   /* a size or index beyond what the library supports     */
+    XD_ENOMEM = 3,   /* device or host allocation failed                       */
+    XD_ECUDA = 4,    /* a CUDA runtime call or kernel failed                   */
+    XD_ESYM = 5,     /* not a group, not a homomorphism, H not invariant       */
+    XD_ENOTCONV = 6  /* Lanczos stopped without meeting its criterion          */
+} xd_status;
+
+typedef enum {
+    XD_F64 = 0,  /* double vectors                                          */
+    XD_F32 = 1,  /* float vectors (storage); products and sums in FP32,
+                    Lanczos dots and alpha/beta in FP64-class arithmetic     */
+    XD_C128 = 2  /* complex double vectors, interleaved (re, im)            */
+} xd_dtype;
+
+/* A finite group of site permutations with a 1-D representation
+ * (Sec. 3.9.1-3.9.2).  perms is [ngroup][N] with perms[g][i] = g(i);
+ * chi_re/chi_im are the characters chi(g).  Validated: every row is a
+ * permutation, the identity is present, the set is closed under
+ * composition and inverses, chi is a homomorphism with |chi| = 1, and
+ * the bond graph (with its couplings) is mapped onto itself. */
+typedef struct {
+    int ngroup;
+    const int32_t *perms;
+    const double *chi_re;
+    const double *chi_im;
+} xd_symmetry;
+
+typedef struct xd_basis_s *xd_basis;
+typedef struct xd_ham_s *xd_ham;
+
+/* ---------------------------------------------------------------- basis */
+
+/* Create the block Spinhalf(N, nup[, irrep]) (Sec. 3.1, Sec. 3.10) for the
+ * interaction graph `bonds` ([nb][2] site pairs, 0-based, i != j, host
+ * memory).  sym == NULL gives the U(1) block.  The graph decides the index
+ * layout; its couplings are set by xd_ham_create.
+ * Limits: 2 <= N <= 40 for U(1) blocks, N <= 40 and ngroup <= 64 for
+ * symmetric ones, 1 <= nb <= 4096, dim < 2^40.  Errors: XD_EINVAL,
+ * XD_ERANGE, XD_ESYM, XD_ENOMEM, XD_ECUDA. */
+xd_status xd_basis_create(int N, int nup, const int32_t *bonds, int nb,
+                          const xd_symmetry *sym, xd_basis *out);
+
+/* Number of basis states (rows of H). */
+xd_status xd_basis_dim(xd_basis b, int64_t *dim);
+
+/* 1 when vectors of this block are complex (a symmetric block whose
+ * characters are not all real), else 0. */
+xd_status xd_basis_is_complex(xd_basis b, int *is_complex);
+
+/* State word of index idx (Sec. 3.1 "index" inverse); XD_ERANGE if out of
+ * range.  Host call, synchronous. */
+xd_status xd_basis_state(xd_basis b, int64_t idx, uint64_t *s);
+
+/* Index of state word s, or -1 when s is not a basis state (for a
+ * symmetric block: s must be a representative).  Host call. */
+xd_status xd_basis_index(xd_basis b, uint64_t s, int64_t *idx);
+
+void xd_basis_destroy(xd_basis b);
+
+/* ---------------------------------------------------------- Hamiltonian */
+
+/* H = sum_b J_b S_i.S_j on basis b (Eq. 1); J is [nb] host doubles.  For a
+ * symmetric block the couplings must be invariant under the group. */
+xd_status xd_ham_create(xd_basis b, const double *J, xd_ham *out);
+
+/* Replace the couplings (same validation as create). */
+xd_status xd_ham_set_couplings(xd_ham h, const double *J);
+
+void xd_ham_destroy(xd_ham h);
+
+/* y = H x (Sec. 3.5 apply; Sec. 5.1 apply_terms with the vector "fill").
+ * x, y: device arrays [dim][nvec] of dtype, distinct, caller-owned.
+ * nvec in {1, 2, 4, 8} (nvec > 1: XD_F32 or XD_F64 on U(1) blocks).
+ * XD_C128 is required on complex blocks; real blocks take XD_F64/XD_F32.
+ * Asynchronous on `stream`. */
+xd_status xd_apply(xd_ham h, const void *x, void *y, xd_dtype dtype,
+                   int nvec, xd_stream stream);
+
+/* Per-bond bilinear forms dJ[b] = Re <g| S_{i_b}.S_{j_b} |x> for every bond
+ * (the J_b-derivative of Re <g|H|x>; Sec. 3.7 inner).  g, x: device [dim]
+ * vectors of dtype (nvec = 1); dJ: device [nb] doubles.  The sum over rows
+ * is deterministic (fixed-order two-stage reduction).  Asynchronous. */
+xd_status xd_apply_bilinear(xd_ham h, const void *g, const void *x,
+                            xd_dtype dtype, double *dJ, xd_stream stream);
+
+/* ---------------------------------------------------------------- Lanczos */
+
+/* Lanczos tridiagonalisation from the seeded normal start vector
+ * (Sec. 3.5 random_state, Sec. 3.6.1 eigvals_lanczos).  Runs at most
+ * max_iter steps, stopping early when beta_k < 1e-13 max|alpha|; vectors
+ * are stored in `storage` (XD_F64, XD_F32, or XD_C128 on complex blocks),
+ * dot products and alpha/beta in FP64-class arithmetic.  Host outputs:
+ * alpha[max_iter], beta[max_iter], *n_iter, evals[nev] (lowest Ritz
+ * values), resid[nev] (|beta_k * last component of the Ritz vector|).
+ * Synchronous.  Device workspace: three vectors of `storage`. */
+xd_status xd_lanczos_eigenvalues(xd_ham h, int max_iter, uint64_t seed,
+                                 xd_dtype storage, int nev, double *alpha,
+                                 double *beta, int *n_iter, double *evals,
+                                 double *resid);
+
+/* As above, then a second Lanczos pass from the same start that rebuilds
+ * the lowest Ritz vector (eig0, Sec. 3.6.1) into psi0 (device, caller-
+ * owned, [dim] of `storage`, unit norm). */
+xd_status xd_lanczos_ground_state(xd_ham h, int max_iter, uint64_t seed,
+                                  xd_dtype storage, int nev, double *alpha,
+                                  double *beta, int *n_iter, double *evals,
+                                  double *resid, void *psi0);
+
+/* dE0/dJ_b = <psi0| S_{i_b}.S_{j_b} |psi0> (Hellmann-Feynman with the
+ * expectation values of Sec. 3.7); psi0 is a device unit vector of dtype;
+ * dEdJ is [nb] host doubles.  Synchronous. */
+xd_status xd_energy_grad(xd_ham h, const void *psi0, xd_dtype dtype,
+                         double *dEdJ);
+
+/* Seeded standard-normal vector, entry i = BoxMuller(SplitMix64(seed ^ 2i),
+ * SplitMix64(seed ^ (2i+1))) (the random_state of Sec. 3.5 with this
+ * project's counter-based generator), unnormalised, written to the device
+ * array out [dim] of dtype (XD_C128: real parts, zero imaginary parts).
+ * Asynchronous. */
+xd_status xd_random_vector(int64_t dim, uint64_t seed, void *out,
+                           xd_dtype dtype, xd_stream stream);
+
+/* ---------------------------------------------------------------- batched */
+
+/* ys[k] = H_k xs[k] for ninst independent U(1) Hamiltonians of uneven size
+ * in one persistent launch (the multi-vector apply of Sec. 5.1 over many
+ * blocks).  xs, ys: host arrays of ninst device pointers, each [dim_k][nvec];
+ * dtype XD_F32 or XD_F64; nvec in {1, 2, 4, 8}.  The tile schedule is chosen
+ * by the library's autotuner on first use of a (set, dtype, nvec) and the
+ * launch is replayed from a captured CUDA graph while the pointers are
+ * unchanged.  Asynchronous. */
+xd_status xd_batch_apply(int ninst, const xd_ham *hs, const void *const *xs,
+                         void *const *ys, xd_dtype dtype, int nvec,
+                         xd_stream stream);
+
+/* Thread-local description of the last error (never NULL). */
+const char *xd_last_error(void);
+
+/* Library version string. */
+const char *xd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XDIAG_GPU_H */

@@ -1,0 +1,142 @@
+// xd_internal.cuh -- shared declarations of the CUDA library (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "xdiag_gpu.h"
+
+namespace xd {
+
+// ------------------------------------------------------------- errors
+void set_error(const char *fmt, ...);
+xd_status cuda_status(cudaError_t e, const char *what);
+
+#define XD_CUDA(call)                                                        \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) return ::xd::cuda_status(e_, #call);          \
+    } while (0)
+
+#define XD_TRY(call)                                                         \
+    do {                                                                     \
+        xd_status s_ = (call);                                               \
+        if (s_ != XD_OK) return s_;                                          \
+    } while (0)
+
+constexpr int kMaxBonds = 4096;
+constexpr int kMaxGroup = 64;
+constexpr int kMaxN = 40;
+
+// ----------------------------------------------------- U(1) index layout
+// A state word s splits into a prefix h = s >> L (P = N - L bits) and a
+// postfix l = s & (2^L - 1).  Rows with the same prefix form one contiguous
+// block (ascending l inside, blocks ascending in h), so
+//     index(s) = hi_off[h] + lo_rank[l]
+// where hi_off[h] is the first row of block h and lo_rank[l] the rank of l
+// among the L-bit words of its popcount (the two Lin tables of Sec. 5.2).
+// lo_list lists the L-bit words sorted by (popcount, value); class m starts
+// at lo_off[m].
+struct U1View {
+    int N, nup, L, P;
+    uint64_t lomask;
+    int64_t dim;
+    const int64_t *hi_off;    // [2^P + 1], hi_off[2^P] = dim
+    const uint32_t *lo_rank;  // [2^L]
+    const uint32_t *lo_list;  // [2^L]
+    const uint32_t *lo_off;   // [L + 2]
+};
+
+// ------------------------------------------------- symmetric block view
+// Representatives ascending; membership of a U(1) word is a rank/select
+// bitmap over U(1) ranks: bit k of bits is set when U(1) state k is a
+// representative in the block, cum[w] counts the set bits before word w.
+struct SymView {
+    int N, G;
+    int64_t dim;
+    const uint64_t *reps;   // [dim]
+    const uint8_t *stab;    // [dim] |Stab(r)|
+    const uint64_t *bits;   // [ceil(dimU1 / 64)]
+    const int64_t *cum;     // [ceil(dimU1 / 64) + 1]
+    const uint64_t *act;    // [G][nchunk][256] byte tables of the action
+    int nchunk;
+    U1View u1;
+};
+
+struct Bond {
+    int i, j;
+};
+
+}  // namespace xd
+
+struct xd_basis_s {
+    int N = 0, nup = 0, nb = 0;
+    std::vector<xd::Bond> bonds;
+    // U(1) layout (always present; a symmetric block uses it for ranks)
+    int L = 0, P = 0;
+    int64_t dim_u1 = 0;
+    std::vector<int64_t> h_hi_off;
+    std::vector<uint32_t> h_lo_rank, h_lo_list, h_lo_off;
+    int64_t *d_hi_off = nullptr;
+    uint32_t *d_lo_rank = nullptr, *d_lo_list = nullptr, *d_lo_off = nullptr;
+    // symmetric block
+    bool sym = false, cplx = false;
+    int G = 0;
+    std::vector<int32_t> perms;
+    std::vector<double> chi_re, chi_im;
+    int64_t dim = 0;
+    uint64_t *d_reps = nullptr;
+    uint8_t *d_stab = nullptr;
+    uint64_t *d_bits = nullptr;
+    int64_t *d_cum = nullptr;
+    uint64_t *d_act = nullptr;
+    int nchunk = 0;
+    double *d_chi = nullptr;  // [G][2]
+
+    xd::U1View u1view() const;
+    xd::SymView symview() const;
+};
+
+struct xd_ham_s {
+    xd_basis b = nullptr;
+    std::vector<double> J;
+    double *d_J = nullptr;          // [nb]
+    double *d_bond = nullptr;       // [J (nb) | bond masks (nb, as uint64) | sum J / 4]
+    double *d_part = nullptr;       // reduction partials
+    size_t part_bytes = 0;
+    double *d_scal = nullptr;       // small device scalars
+    double *d_lzpart = nullptr;     // Lanczos reduction partials
+    int lzpart_n = 0;
+    double *d_symtab = nullptr;     // symmetric blocks: sqrt ratios [(G+1)^2] | bond orbit ids
+};
+
+namespace xd {
+
+// ------------------------------------------------------------ kernels
+// U(1) product (xd_u1.cu)
+xd_status u1_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt,
+                   int nvec, cudaStream_t st);
+xd_status u1_bilinear(const xd_ham_s *h, const void *g, const void *x,
+                      xd_dtype dt, double *dJ, cudaStream_t st);
+// symmetric blocks (xd_sym.cu)
+xd_status sym_build(xd_basis_s *b);
+xd_status sym_ham_tables(xd_ham_s *h);
+xd_status sym_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt,
+                    cudaStream_t st);
+xd_status sym_bilinear(const xd_ham_s *h, const void *g, const void *x,
+                       xd_dtype dt, double *dJ, cudaStream_t st);
+// vector kernels (xd_vec.cu)
+xd_status vec_random(int64_t n, uint64_t seed, void *out, xd_dtype dt,
+                     cudaStream_t st);
+// forget cached batch plans that use this handle (xd_batch.cu)
+void batch_forget(const xd_ham_s *h);
+// workspace helper
+xd_status ensure_partials(xd_ham_s *h, size_t bytes);
+
+int grid_for(int64_t work, int threads, int per_sm);
+extern int g_num_sms;
+
+}  // namespace xd

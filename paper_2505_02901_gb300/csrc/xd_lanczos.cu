@@ -1,0 +1,479 @@
+// xd_lanczos.cu -- seeded start vectors, fused vector kernels, the Lanczos
+// driver (eigvals_lanczos / eig0 of Sec. 3.6.1) and the host tridiagonal
+// eigensolver (a6, a7).
+//
+// Krylov vectors are kept unnormalised with a host scale sigma_k so that
+// v_k = sigma_k u_k; one step is
+//     w     = H u_k                                   (xd_apply)
+//     w     = sigma_k w - beta_{k-1} sigma_{k-1} u_{k-1},  alpha_k = sigma_k <w, u_k>
+//     w     = w - alpha_k sigma_k u_k,                beta_k = ||w||
+//     u_{k+1} = w, sigma_{k+1} = 1 / beta_k.
+// Complex vectors with real scalars are real vectors of twice the length,
+// and alpha = Re <v, Hv> for Hermitian H, so the same kernels serve them.
+// Dot products: FP64 fused multiply-adds for double storage; for float
+// storage each thread keeps an exact float product split (FMA) and a
+// compensated float pair sum (FP64-class), and partial sums meet in FP64.
+// All reductions run in a fixed order (per-CTA partials, then one pass).
+
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "xd_internal.cuh"
+
+namespace xd {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <typename T>
+__global__ void k_random(int64_t n, uint64_t seed, T *__restrict__ out, int stride) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t a = splitmix64(seed ^ (2ull * (uint64_t)i));
+        const uint64_t b = splitmix64(seed ^ (2ull * (uint64_t)i + 1ull));
+        const double u1 = ((double)(a >> 11) + 1.0) * 0x1.0p-53;
+        const double u2 = ((double)(b >> 11) + 1.0) * 0x1.0p-53;
+        const double v = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+        out[i * stride] = (T)v;
+        if (stride == 2) out[i * stride + 1] = (T)0;
+    }
+}
+
+struct AccD {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double get() const { return s; }
+};
+
+// Exact product split and compensated sum in float pairs.
+struct AccF {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float pe = fmaf(a, b, -p);             // a*b = p + pe exactly
+        const float s = __fadd_rn(hi, p);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(e, pe));
+    }
+    __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+};
+
+template <typename T>
+struct AccOf;
+template <>
+struct AccOf<double> {
+    using A = AccD;
+};
+template <>
+struct AccOf<float> {
+    using A = AccF;
+};
+
+// block-wide sum of one double per thread into part[blockIdx.x] (fixed order)
+__device__ __forceinline__ void block_store(double v, double *__restrict__ part) {
+    __shared__ double red[kThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        part[blockIdx.x] = s;
+    }
+}
+
+// w = a w + c z (z may be NULL);  part = <w, v> (v may be NULL: no dot)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_axpby_dot(int64_t n, T *__restrict__ w, T a,
+                                                        const T *__restrict__ z, T c,
+                                                        const T *__restrict__ v,
+                                                        double *__restrict__ part) {
+    typename AccOf<T>::A acc;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        T t = a * w[i];
+        if (z) t += c * z[i];
+        w[i] = t;
+        if (v) acc.add(t, v[i]);
+    }
+    if (part) block_store(acc.get(), part);
+}
+
+// psi += c u
+template <typename T>
+__global__ void k_axpy(int64_t n, T *__restrict__ psi, T c, const T *__restrict__ u) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        psi[i] += c * u[i];
+}
+
+__global__ void k_sum(const double *__restrict__ part, int n, double *__restrict__ out) {
+    if (threadIdx.x || blockIdx.x) return;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    *out = s;
+}
+
+}  // namespace
+
+xd_status vec_random(int64_t n, uint64_t seed, void *out, xd_dtype dt, cudaStream_t st) {
+    if (n == 0) return XD_OK;
+    int grid = grid_for(n, kThreads, 16);
+    if (dt == XD_F32) k_random<float><<<grid, kThreads, 0, st>>>(n, seed, (float *)out, 1);
+    else k_random<double><<<grid, kThreads, 0, st>>>(n, seed, (double *)out, dt == XD_C128 ? 2 : 1);
+    XD_CUDA(cudaGetLastError());
+    return XD_OK;
+}
+
+// ------------------------------------------------------------ host side
+
+// Number of eigenvalues of the symmetric tridiagonal (d, e) below x
+// (Sturm sequence of the LDL^T pivots).
+static int sturm_count(int n, const double *d, const double *e, double x) {
+    int cnt = 0;
+    double q = 1.0;
+    for (int i = 0; i < n; ++i) {
+        double e2 = i ? e[i - 1] * e[i - 1] : 0.0;
+        q = d[i] - x - (i ? e2 / q : 0.0);
+        if (q == 0.0) q = -1e-300;  // treat an exact zero pivot as negative
+        if (q < 0) ++cnt;
+    }
+    return cnt;
+}
+
+// k-th smallest eigenvalue (0-based) by bisection on the Sturm count.
+static double tridiag_eig(int n, const double *d, const double *e, int k) {
+    double lo = d[0], hi = d[0];
+    for (int i = 0; i < n; ++i) {
+        double r = (i ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+        lo = std::min(lo, d[i] - r);
+        hi = std::max(hi, d[i] + r);
+    }
+    double scale = std::max(fabs(lo), fabs(hi)) + 1e-300;
+    lo -= 1e-12 * scale;
+    hi += 1e-12 * scale;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (sturm_count(n, d, e, mid) > k) hi = mid; else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Eigenvector of (d, e) for eigenvalue lam by inverse iteration on
+// (T - mu I) z = b with a pivoted tridiagonal LU (three sweeps).
+static void tridiag_vec(int n, const double *d, const double *e, double lam, double *z) {
+    if (n == 1) {
+        z[0] = 1.0;
+        return;
+    }
+    double norm = 0.0;
+    for (int i = 0; i < n; ++i) norm = std::max(norm, fabs(d[i]) + (i ? fabs(e[i - 1]) : 0) + (i < n - 1 ? fabs(e[i]) : 0));
+    const double mu = lam + 1e-14 * (norm + 1e-300);
+    // banded LU with partial pivoting: row i has entries at columns i..i+2 after pivoting
+    std::vector<double> u0(n), u1(n), u2(n), l(n);
+    std::vector<char> swp(n, 0);
+    // current row i: (a = diag, b = super), next row: (c = sub, dd = diag, ee = super)
+    double a = d[0] - mu, b = n > 1 ? e[0] : 0.0;
+    double b2 = 0.0;
+    for (int i = 0; i < n - 1; ++i) {
+        double c = e[i], dd = d[i + 1] - mu, ee = (i + 2 < n) ? e[i + 1] : 0.0;
+        if (fabs(c) > fabs(a)) {  // swap rows i and i+1
+            swp[i] = 1;
+            u0[i] = c;
+            u1[i] = dd;
+            u2[i] = ee;
+            double m = a / c;
+            l[i] = m;
+            a = b - m * dd;
+            b = b2 - m * ee;
+            b2 = 0.0;
+        } else {
+            swp[i] = 0;
+            u0[i] = a;
+            u1[i] = b;
+            u2[i] = b2;
+            double m = (a != 0.0) ? c / a : 0.0;
+            l[i] = m;
+            a = dd - m * b;
+            b = ee - m * b2;
+            b2 = 0.0;
+        }
+    }
+    u0[n - 1] = (a != 0.0) ? a : 1e-300;
+    u1[n - 1] = 0.0;
+    u2[n - 1] = 0.0;
+    std::vector<double> rhs(n, 1.0);
+    for (int sweep = 0; sweep < 3; ++sweep) {
+        // forward: apply the row swaps and multipliers
+        std::vector<double> y(rhs);
+        for (int i = 0; i < n - 1; ++i) {
+            if (swp[i]) std::swap(y[i], y[i + 1]);
+            y[i + 1] -= l[i] * y[i];
+        }
+        // back substitution
+        for (int i = n - 1; i >= 0; --i) {
+            double s = y[i];
+            if (i + 1 < n) s -= u1[i] * z[i + 1];
+            if (i + 2 < n) s -= u2[i] * z[i + 2];
+            double piv = u0[i] != 0.0 ? u0[i] : 1e-300;
+            z[i] = s / piv;
+        }
+        double nz = 0.0;
+        for (int i = 0; i < n; ++i) nz += z[i] * z[i];
+        nz = sqrt(nz);
+        for (int i = 0; i < n; ++i) {
+            z[i] /= nz;
+            rhs[i] = z[i];
+        }
+    }
+    // fix the sign: first non-negligible component positive
+    for (int i = 0; i < n; ++i)
+        if (fabs(z[i]) > 1e-8) {
+            if (z[i] < 0)
+                for (int k = 0; k < n; ++k) z[k] = -z[k];
+            break;
+        }
+}
+
+static xd_status ensure_lanczos_partials(xd_ham_s *h, int n) {
+    if (h->lzpart_n >= n) return XD_OK;
+    cudaFree(h->d_lzpart);
+    h->d_lzpart = nullptr;
+    h->lzpart_n = 0;
+    XD_CUDA(cudaMalloc((void **)&h->d_lzpart, sizeof(double) * n));
+    h->lzpart_n = n;
+    return XD_OK;
+}
+
+struct LzWork {
+    void *u_prev, *u, *w;
+    double *part, *scal;
+    int grid;
+};
+
+template <typename T>
+static xd_status lz_axpby(int64_t n, T *w, double a, const T *z, double c, const T *v,
+                          const LzWork &lw, cudaStream_t st, double *dot) {
+    k_axpby_dot<T><<<lw.grid, kThreads, 0, st>>>(n, w, (T)a, z, (T)c, v, v ? lw.part : nullptr);
+    XD_CUDA(cudaGetLastError());
+    if (dot) {
+        k_sum<<<1, 32, 0, st>>>(lw.part, lw.grid, lw.scal);
+        XD_CUDA(cudaGetLastError());
+        XD_CUDA(cudaMemcpyAsync(dot, lw.scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+        XD_CUDA(cudaStreamSynchronize(st));
+    }
+    return XD_OK;
+}
+
+// One Lanczos run.  With coef != NULL it is the second pass: it reuses the
+// recorded alpha/beta and accumulates psi = sum_k coef[k] v_k.
+template <typename T>
+static xd_status lanczos_run(xd_ham_s *h, int max_iter, uint64_t seed, xd_dtype dt, double *alpha,
+                             double *beta, int *n_iter, const double *coef, T *psi) {
+    const xd_basis_s *b = h->b;
+    const int64_t n = b->dim * (b->cplx ? 2 : 1);
+    cudaStream_t st = 0;
+    LzWork lw;
+    lw.grid = grid_for(n, kThreads, 8);
+    const size_t vbytes = (size_t)n * sizeof(T);
+    XD_TRY(ensure_lanczos_partials(h, lw.grid));
+    lw.part = h->d_lzpart;
+    lw.scal = h->d_scal;
+    T *buf[3] = {nullptr, nullptr, nullptr};
+    for (int k = 0; k < 3; ++k) {
+        cudaError_t e = cudaMalloc((void **)&buf[k], std::max<size_t>(vbytes, 16));
+        if (e != cudaSuccess) {
+            for (int q = 0; q < k; ++q) cudaFree(buf[q]);
+            return cuda_status(e, "cudaMalloc(Lanczos vectors)");
+        }
+    }
+    xd_status rc = XD_OK;
+    T *up = buf[0], *u = buf[1], *w = buf[2];
+    do {
+        if ((rc = vec_random(b->dim, seed, u, dt, st)) != XD_OK) break;
+        cudaError_t e0 = cudaMemsetAsync(up, 0, vbytes, st);
+        if (e0 != cudaSuccess) {
+            rc = cuda_status(e0, "cudaMemsetAsync");
+            break;
+        }
+        double nrm2 = 0.0;
+        if ((rc = lz_axpby<T>(n, u, 1.0, nullptr, 0.0, u, lw, st, &nrm2)) != XD_OK) break;
+        if (!(nrm2 > 0.0)) {
+            set_error("Lanczos: zero start vector");
+            rc = XD_EINVAL;
+            break;
+        }
+        double sig = 1.0 / sqrt(nrm2), sig_prev = 0.0, beta_prev = 0.0, amax = 0.0;
+        int k = 0;
+        const int steps = coef ? *n_iter : max_iter;
+        for (k = 0; k < steps; ++k) {
+            if (coef) {
+                k_axpy<T><<<lw.grid, kThreads, 0, st>>>(n, psi, (T)(coef[k] * sig), u);
+                cudaError_t e = cudaGetLastError();
+                if (e != cudaSuccess) {
+                    rc = cuda_status(e, "k_axpy");
+                    break;
+                }
+                if (k == steps - 1) break;
+                if ((rc = xd_apply(h, u, w, dt, 1, (xd_stream)st)) != XD_OK) break;
+                if ((rc = lz_axpby<T>(n, w, sig, up, -beta_prev * sig_prev, nullptr, lw, st, nullptr)) != XD_OK) break;
+                if ((rc = lz_axpby<T>(n, w, 1.0, u, -alpha[k] * sig, nullptr, lw, st, nullptr)) != XD_OK) break;
+                beta_prev = beta[k];
+            } else {
+                if ((rc = xd_apply(h, u, w, dt, 1, (xd_stream)st)) != XD_OK) break;
+                double d1 = 0.0, d2 = 0.0;
+                if ((rc = lz_axpby<T>(n, w, sig, up, -beta_prev * sig_prev, u, lw, st, &d1)) != XD_OK) break;
+                const double a = sig * d1;
+                if ((rc = lz_axpby<T>(n, w, 1.0, u, -a * sig, w, lw, st, &d2)) != XD_OK) break;
+                const double bt = sqrt(std::max(d2, 0.0));
+                alpha[k] = a;
+                beta[k] = bt;
+                amax = std::max(amax, fabs(a));
+                beta_prev = bt;
+                if (bt < 1e-13 * amax || k == steps - 1) {
+                    ++k;
+                    break;
+                }
+            }
+            sig_prev = sig;
+            sig = 1.0 / beta_prev;
+            T *t = up;
+            up = u;
+            u = w;
+            w = t;
+        }
+        if (rc != XD_OK) break;
+        if (!coef) *n_iter = k;
+    } while (0);
+    cudaError_t e = cudaStreamSynchronize(st);
+    for (int q = 0; q < 3; ++q) cudaFree(buf[q]);
+    if (rc == XD_OK && e != cudaSuccess) rc = cuda_status(e, "Lanczos");
+    return rc;
+}
+
+static xd_status check_lanczos_args(xd_ham h, int max_iter, xd_dtype dt, int nev, double *alpha,
+                                    double *beta, int *n_iter, double *evals, double *resid) {
+    if (!h || !alpha || !beta || !n_iter || !evals || !resid) {
+        set_error("xd_lanczos: NULL argument");
+        return XD_EINVAL;
+    }
+    if (max_iter < 1 || nev < 1) {
+        set_error("xd_lanczos: need max_iter >= 1 and nev >= 1");
+        return XD_EINVAL;
+    }
+    const xd_basis_s *b = h->b;
+    if (b->dim == 0) {
+        set_error("xd_lanczos: empty block");
+        return XD_EINVAL;
+    }
+    if (b->cplx ? dt != XD_C128 : (dt != XD_F64 && (dt != XD_F32 || b->sym))) {
+        set_error("xd_lanczos: storage dtype %d not valid for this block", (int)dt);
+        return XD_EINVAL;
+    }
+    return XD_OK;
+}
+
+static void ritz(int n, const double *alpha, const double *beta, int nev, double *evals,
+                 double *resid, std::vector<double> *z0) {
+    std::vector<double> z(n);
+    for (int j = 0; j < nev; ++j) {
+        if (j >= n) {
+            evals[j] = NAN;
+            resid[j] = NAN;
+            continue;
+        }
+        evals[j] = tridiag_eig(n, alpha, beta, j);
+        tridiag_vec(n, alpha, beta, evals[j], z.data());
+        resid[j] = fabs(beta[n - 1] * z[n - 1]);
+        if (j == 0 && z0) *z0 = z;
+    }
+}
+
+}  // namespace xd
+
+using namespace xd;
+
+extern "C" {
+
+xd_status xd_lanczos_eigenvalues(xd_ham h, int max_iter, uint64_t seed, xd_dtype dt, int nev,
+                                 double *alpha, double *beta, int *n_iter, double *evals,
+                                 double *resid) {
+    XD_TRY(check_lanczos_args(h, max_iter, dt, nev, alpha, beta, n_iter, evals, resid));
+    xd_status s = (dt == XD_F32)
+                      ? lanczos_run<float>(h, max_iter, seed, dt, alpha, beta, n_iter, nullptr, nullptr)
+                      : lanczos_run<double>(h, max_iter, seed, dt, alpha, beta, n_iter, nullptr, nullptr);
+    if (s != XD_OK) return s;
+    ritz(*n_iter, alpha, beta, nev, evals, resid, nullptr);
+    return XD_OK;
+}
+
+xd_status xd_lanczos_ground_state(xd_ham h, int max_iter, uint64_t seed, xd_dtype dt, int nev,
+                                  double *alpha, double *beta, int *n_iter, double *evals,
+                                  double *resid, void *psi0) {
+    XD_TRY(check_lanczos_args(h, max_iter, dt, nev, alpha, beta, n_iter, evals, resid));
+    if (!psi0) {
+        set_error("xd_lanczos_ground_state: psi0 is NULL");
+        return XD_EINVAL;
+    }
+    XD_TRY(xd_lanczos_eigenvalues(h, max_iter, seed, dt, nev, alpha, beta, n_iter, evals, resid));
+    std::vector<double> c;
+    ritz(*n_iter, alpha, beta, 1, evals, resid, &c);
+    const xd_basis_s *b = h->b;
+    const int64_t n = b->dim * (b->cplx ? 2 : 1);
+    const size_t vbytes = (size_t)n * (dt == XD_F32 ? 4 : 8);
+    XD_CUDA(cudaMemset(psi0, 0, vbytes));
+    xd_status s = (dt == XD_F32)
+                      ? lanczos_run<float>(h, max_iter, seed, dt, alpha, beta, n_iter, c.data(), (float *)psi0)
+                      : lanczos_run<double>(h, max_iter, seed, dt, alpha, beta, n_iter, c.data(), (double *)psi0);
+    if (s != XD_OK) return s;
+    // normalise
+    LzWork lw;
+    lw.grid = grid_for(n, kThreads, 8);
+    XD_TRY(ensure_lanczos_partials(h, lw.grid));
+    lw.part = h->d_lzpart;
+    lw.scal = h->d_scal;
+    double nrm2 = 0.0;
+    if (dt == XD_F32) {
+        XD_TRY(lz_axpby<float>(n, (float *)psi0, 1.0, nullptr, 0.0, (float *)psi0, lw, 0, &nrm2));
+        XD_TRY(lz_axpby<float>(n, (float *)psi0, 1.0 / sqrt(nrm2), nullptr, 0.0, nullptr, lw, 0, nullptr));
+    } else {
+        XD_TRY(lz_axpby<double>(n, (double *)psi0, 1.0, nullptr, 0.0, (double *)psi0, lw, 0, &nrm2));
+        XD_TRY(lz_axpby<double>(n, (double *)psi0, 1.0 / sqrt(nrm2), nullptr, 0.0, nullptr, lw, 0, nullptr));
+    }
+    XD_CUDA(cudaDeviceSynchronize());
+    return XD_OK;
+}
+
+xd_status xd_energy_grad(xd_ham h, const void *psi0, xd_dtype dt, double *dEdJ) {
+    if (!h || !psi0 || !dEdJ) {
+        set_error("xd_energy_grad: NULL argument");
+        return XD_EINVAL;
+    }
+    const int nb = h->b->nb;
+    double *d_out = nullptr;
+    XD_CUDA(cudaMalloc((void **)&d_out, sizeof(double) * nb));
+    xd_status s = xd_apply_bilinear(h, psi0, psi0, dt, d_out, nullptr);
+    if (s == XD_OK) {
+        cudaError_t e = cudaMemcpy(dEdJ, d_out, sizeof(double) * nb, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) s = cuda_status(e, "xd_energy_grad copy");
+    }
+    cudaFree(d_out);
+    return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,513 @@
+// xd_sym.cu -- symmetry-adapted blocks of a site-permutation group.
+//
+// Basis (Sec. 3.10): the representative of an orbit is its smallest word;
+// a representative r stays in the block of a 1-D representation chi when
+// sum_{g in Stab(r)} chi(g) != 0.  The block is built on the device: every
+// U(1) word is tested (a1 over the U(1) layout), the members are marked in a
+// rank/select bitmap over U(1) ranks and compacted into the ascending
+// representative list.
+//
+// Product (a4', derived from the projector of Sec. 3.10): with
+// |r_chi> = (1/N_r) sum_g conj(chi(g)) g|r>, N_r = sqrt(|G| |Stab(r)|), the
+// pull form of row r is
+//     y_r = d(r) x_r + sum_{flips t} (J_b/2) chi(u_t) sqrt(|Stab(r'_t)|/|Stab(r)|) x_{r'_t}
+// where r'_t = min_g g s_t is the representative of the flipped word s_t,
+// u_t any element with u_t s_t = r'_t, and a target whose representative is
+// not in the block contributes nothing.  The index of r'_t is its U(1) rank
+// (two-table layout) followed by a rank/select lookup in the bitmap.
+
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "xd_internal.cuh"
+
+namespace xd {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// g s through byte tables: tab[g][c][v] is the image of the bits v << 8c.
+__device__ __forceinline__ uint64_t act(const uint64_t *__restrict__ tab, int nchunk, int g,
+                                        uint64_t s) {
+    const uint64_t *t = tab + (size_t)g * nchunk * 256;
+    uint64_t r = 0;
+    for (int c = 0; c < nchunk; ++c) r |= __ldg(t + c * 256 + ((s >> (8 * c)) & 255));
+    return r;
+}
+
+struct Orbit {
+    uint64_t rep;  // smallest image
+    int u;         // first g reaching it
+    int cnt;       // number of g reaching it = |Stab(rep)|
+};
+
+__device__ __forceinline__ Orbit orbit_min(const SymView &v, uint64_t s) {
+    Orbit o{~0ull, 0, 0};
+    for (int g = 0; g < v.G; ++g) {
+        uint64_t t = act(v.act, v.nchunk, g, s);
+        if (t < o.rep) {
+            o.rep = t;
+            o.u = g;
+            o.cnt = 1;
+        } else if (t == o.rep) {
+            ++o.cnt;
+        }
+    }
+    return o;
+}
+
+__device__ __forceinline__ uint64_t find_block(const int64_t *__restrict__ hi_off, uint64_t lo,
+                                               uint64_t hi, int64_t r) {
+    while (lo < hi) {
+        uint64_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(hi_off + mid) <= r) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint64_t u1_state(const U1View &u, int64_t k, uint64_t &h) {
+    // h: a lower bound hint for the block (updated)
+    while (__ldg(u.hi_off + h + 1) <= k) ++h;
+    int m = u.nup - __popcll(h);
+    uint32_t l = __ldg(u.lo_list + __ldg(u.lo_off + m) + (uint32_t)(k - __ldg(u.hi_off + h)));
+    return (h << u.L) | l;
+}
+
+// Membership test of the 64 U(1) states of word w.
+__device__ uint64_t member_word(const SymView &v, const double *__restrict__ chi, int64_t w,
+                                int *nmem) {
+    const U1View &u = v.u1;
+    int64_t k0 = w * 64, k1 = min(k0 + 64, u.dim);
+    uint64_t h = find_block(u.hi_off, 0, (1ull << u.P) - 1, k0);
+    uint64_t bits = 0;
+    for (int64_t k = k0; k < k1; ++k) {
+        uint64_t s = u1_state(u, k, h);
+        double cr = 0.0, ci = 0.0;
+        bool is_rep = true;
+        for (int g = 0; g < v.G && is_rep; ++g) {
+            uint64_t t = act(v.act, v.nchunk, g, s);
+            if (t < s) is_rep = false;
+            if (t == s) {
+                cr += chi[2 * g];
+                ci += chi[2 * g + 1];
+            }
+        }
+        if (is_rep && cr * cr + ci * ci > 0.25) bits |= 1ull << (k - k0);
+    }
+    *nmem = __popcll(bits);
+    return bits;
+}
+
+__global__ void k_mark(SymView v, const double *__restrict__ chi, int64_t nwords,
+                       uint64_t *__restrict__ bits, int64_t *__restrict__ cnt) {
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        int n;
+        bits[w] = member_word(v, chi, w, &n);
+        cnt[w] = n;
+    }
+}
+
+__global__ void k_compact(SymView v, int64_t nwords, const uint64_t *__restrict__ bits,
+                          const int64_t *__restrict__ cum, uint64_t *__restrict__ reps,
+                          uint8_t *__restrict__ stab) {
+    const U1View &u = v.u1;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t b = bits[w];
+        if (!b) continue;
+        int64_t k0 = w * 64;
+        uint64_t h = find_block(u.hi_off, 0, (1ull << u.P) - 1, k0);
+        int64_t out = cum[w];
+        while (b) {
+            int j = __ffsll((long long)b) - 1;
+            b &= b - 1;
+            uint64_t s = u1_state(u, k0 + j, h);
+            int c = 0;
+            for (int g = 0; g < v.G; ++g) c += act(v.act, v.nchunk, g, s) == s;
+            reps[out] = s;
+            stab[out] = (uint8_t)c;
+            ++out;
+        }
+    }
+}
+
+// ---- exclusive scan of int64 counts (three phases, fixed order)
+constexpr int kScanChunk = 4096;
+
+__global__ void k_scan_sums(const int64_t *__restrict__ in, int64_t n, int64_t *__restrict__ sums) {
+    __shared__ int64_t red[kThreads];
+    int64_t base = (int64_t)blockIdx.x * kScanChunk;
+    int64_t s = 0;
+    for (int64_t i = base + threadIdx.x; i < min(base + kScanChunk, n); i += blockDim.x) s += in[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[blockIdx.x] = red[0];
+}
+
+__global__ void k_scan_serial(int64_t *__restrict__ sums, int64_t n) {
+    if (threadIdx.x || blockIdx.x) return;
+    int64_t run = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t t = sums[i];
+        sums[i] = run;
+        run += t;
+    }
+    sums[n] = run;
+}
+
+__global__ void k_scan_apply(const int64_t *__restrict__ in, int64_t n,
+                             const int64_t *__restrict__ sums, int64_t *__restrict__ out) {
+    // one thread walks a sub-chunk; the block scans the sub-chunk totals
+    __shared__ int64_t part[kThreads + 1];
+    const int per = kScanChunk / kThreads;
+    int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * per;
+    int64_t s = 0;
+    for (int k = 0; k < per; ++k)
+        if (base + k < n) s += in[base + k];
+    part[threadIdx.x + 1] = s;
+    if (threadIdx.x == 0) part[0] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int t = 1; t <= kThreads; ++t) part[t] += part[t - 1];
+    __syncthreads();
+    int64_t run = sums[blockIdx.x] + part[threadIdx.x];
+    for (int k = 0; k < per; ++k)
+        if (base + k < n) {
+            out[base + k] = run;
+            run += in[base + k];
+        }
+}
+
+template <bool CPLX>
+struct Val;
+template <>
+struct Val<false> {
+    using T = double;
+};
+template <>
+struct Val<true> {
+    using T = double2;
+};
+
+// Row r of y = H x (see the file header).  sq[a][m] = sqrt(a / m).
+template <bool CPLX>
+__global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, const double *__restrict__ bond,
+                                                        int nb, const double *__restrict__ chi,
+                                                        const double *__restrict__ sq,
+                                                        const typename Val<CPLX>::T *__restrict__ x,
+                                                        typename Val<CPLX>::T *__restrict__ y) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *sm_mask = (uint64_t *)smem;
+    double *sm_half = (double *)(sm_mask + nb);
+    double *sm_chi = sm_half + nb;          // [G][2]
+    double *sm_sq = sm_chi + 2 * v.G;       // [(G+1)^2]
+    const uint64_t *masks = (const uint64_t *)(bond + nb);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        sm_half[b] = 0.5 * bond[b];
+        sm_mask[b] = masks[b];
+    }
+    for (int g = threadIdx.x; g < 2 * v.G; g += blockDim.x) sm_chi[g] = chi[g];
+    for (int q = threadIdx.x; q < (v.G + 1) * (v.G + 1); q += blockDim.x) sm_sq[q] = sq[q];
+    const double jq = bond[2 * nb];
+    __syncthreads();
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < v.dim;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t s = __ldg(v.reps + r);
+        const int mr = __ldg(v.stab + r);
+        double ar = 0.0, ai = 0.0, dsub = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            const uint64_t mk = sm_mask[b];
+            const uint64_t t = s & mk;
+            if (t == 0 || t == mk) continue;
+            const double hb = sm_half[b];
+            dsub += hb;
+            const Orbit o = orbit_min(v, s ^ mk);
+            const int64_t k = __ldg(v.u1.hi_off + (o.rep >> v.u1.L)) +
+                              (int64_t)__ldg(v.u1.lo_rank + (o.rep & v.u1.lomask));
+            const uint64_t word = __ldg(v.bits + (k >> 6));
+            if (!((word >> (k & 63)) & 1)) continue;
+            const int64_t c = __ldg(v.cum + (k >> 6)) + __popcll(word & ((1ull << (k & 63)) - 1));
+            const double a = hb * sm_sq[o.cnt * (v.G + 1) + mr];
+            if constexpr (CPLX) {
+                const double2 xc = x[c];
+                const double cr = a * sm_chi[2 * o.u], ci = a * sm_chi[2 * o.u + 1];
+                ar += cr * xc.x - ci * xc.y;
+                ai += cr * xc.y + ci * xc.x;
+            } else {
+                ar += a * sm_chi[2 * o.u] * x[c];
+            }
+        }
+        const double d = jq - dsub;
+        if constexpr (CPLX) {
+            const double2 xr = x[r];
+            y[r] = make_double2(d * xr.x + ar, d * xr.y + ai);
+        } else {
+            y[r] = d * x[r] + ar;
+        }
+    }
+}
+
+// Per-bond contributions C(b) = Re sum_r conj(g_r) [bond-b part of row r],
+// reduced per CTA into part[cta][b] (fixed order).
+constexpr int kChunk = 128;
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kThreads) k_sym_bilinear(SymView v, const uint64_t *__restrict__ masks,
+                                                           int nb, int b0, const double *__restrict__ chi,
+                                                           const double *__restrict__ sq,
+                                                           const typename Val<CPLX>::T *__restrict__ g,
+                                                           const typename Val<CPLX>::T *__restrict__ x,
+                                                           double *__restrict__ part) {
+    __shared__ double acc[kThreads / 32][kChunk];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nbc = min(kChunk, nb - b0);
+    for (int b = lane; b < nbc; b += 32) acc[warp][b] = 0.0;
+    __syncwarp();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t rounds = (v.dim + stride - 1) / stride;
+    for (int64_t it = 0; it < rounds; ++it) {
+        const int64_t r = it * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const bool valid = r < v.dim;
+        uint64_t s = 0;
+        int mr = 1;
+        double gr = 0, gi = 0, xr = 0, xi = 0;
+        if (valid) {
+            s = v.reps[r];
+            mr = v.stab[r];
+            if constexpr (CPLX) {
+                gr = g[r].x; gi = g[r].y; xr = x[r].x; xi = x[r].y;
+            } else {
+                gr = g[r]; xr = x[r];
+            }
+        }
+        for (int b = 0; b < nbc; ++b) {
+            double val = 0.0;
+            if (valid) {
+                const uint64_t mk = masks[b0 + b];
+                const uint64_t t = s & mk;
+                // Re conj(g_r) * (term) ; diagonal term is +-1/4 x_r
+                const double diag = (t == 0 || t == mk) ? 0.25 : -0.25;
+                val = diag * (gr * xr + gi * xi);
+                if (!(t == 0 || t == mk)) {
+                    const Orbit o = orbit_min(v, s ^ mk);
+                    const int64_t k = __ldg(v.u1.hi_off + (o.rep >> v.u1.L)) +
+                                      (int64_t)__ldg(v.u1.lo_rank + (o.rep & v.u1.lomask));
+                    const uint64_t word = __ldg(v.bits + (k >> 6));
+                    if ((word >> (k & 63)) & 1) {
+                        const int64_t c = __ldg(v.cum + (k >> 6)) +
+                                          __popcll(word & ((1ull << (k & 63)) - 1));
+                        const double a = 0.5 * sq[o.cnt * (v.G + 1) + mr];
+                        const double cr = a * chi[2 * o.u], ci = a * chi[2 * o.u + 1];
+                        double tr, ti;
+                        if constexpr (CPLX) {
+                            tr = cr * x[c].x - ci * x[c].y;
+                            ti = cr * x[c].y + ci * x[c].x;
+                        } else {
+                            tr = cr * x[c];
+                            ti = ci * x[c];
+                        }
+                        val += gr * tr + gi * ti;
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+            if (lane == 0) acc[warp][b] += val;
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbc; b += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) s += acc[w][b];
+        part[(size_t)blockIdx.x * nb + b0 + b] = s;
+    }
+}
+
+// dJ[b] = mean over the bond orbit of sum_c part[c][b']
+__global__ void k_orbit_mean(const double *__restrict__ part, int rows, int nb,
+                             const int32_t *__restrict__ orbit, double *__restrict__ out) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    double s = 0.0;
+    int n = 0;
+    for (int q = 0; q < nb; ++q) {
+        if (orbit[q] != orbit[b]) continue;
+        ++n;
+        for (int c = 0; c < rows; ++c) s += part[(size_t)c * nb + q];
+    }
+    out[b] = s / n;
+}
+
+}  // namespace
+
+static xd_status make_tables(xd_basis_s *b) {
+    const int N = b->N, G = b->G;
+    b->nchunk = (N + 7) / 8;
+    std::vector<uint64_t> tab((size_t)G * b->nchunk * 256, 0);
+    for (int g = 0; g < G; ++g) {
+        const int32_t *p = b->perms.data() + (size_t)g * N;
+        std::vector<int> inv(N);
+        for (int i = 0; i < N; ++i) inv[p[i]] = i;  // bit j of s lands on bit inv[j]
+        for (int c = 0; c < b->nchunk; ++c)
+            for (int val = 0; val < 256; ++val) {
+                uint64_t r = 0;
+                for (int k = 0; k < 8; ++k) {
+                    int j = 8 * c + k;
+                    if (j < N && ((val >> k) & 1)) r |= 1ull << inv[j];
+                }
+                tab[((size_t)g * b->nchunk + c) * 256 + val] = r;
+            }
+    }
+    XD_CUDA(cudaMalloc((void **)&b->d_act, tab.size() * sizeof(uint64_t)));
+    XD_CUDA(cudaMemcpy(b->d_act, tab.data(), tab.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
+    std::vector<double> chi(2 * G);
+    for (int g = 0; g < G; ++g) {
+        chi[2 * g] = b->chi_re[g];
+        chi[2 * g + 1] = b->chi_im[g];
+    }
+    XD_CUDA(cudaMalloc((void **)&b->d_chi, chi.size() * sizeof(double)));
+    XD_CUDA(cudaMemcpy(b->d_chi, chi.data(), chi.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return XD_OK;
+}
+
+xd_status sym_build(xd_basis_s *b) {
+    XD_TRY(make_tables(b));
+    const int64_t nwords = (b->dim_u1 + 63) / 64;
+    XD_CUDA(cudaMalloc((void **)&b->d_bits, std::max<int64_t>(1, nwords) * sizeof(uint64_t)));
+    XD_CUDA(cudaMalloc((void **)&b->d_cum, (nwords + 1) * sizeof(int64_t)));
+    int64_t *cnt = nullptr, *sums = nullptr;
+    const int64_t nchunks = (nwords + kScanChunk - 1) / kScanChunk;
+    XD_CUDA(cudaMalloc((void **)&cnt, std::max<int64_t>(1, nwords) * sizeof(int64_t)));
+    cudaError_t e = cudaMalloc((void **)&sums, (nchunks + 1) * sizeof(int64_t));
+    if (e != cudaSuccess) {
+        cudaFree(cnt);
+        return cuda_status(e, "cudaMalloc(scan)");
+    }
+    SymView v = b->symview();
+    int grid = grid_for(nwords, kThreads, 16);
+    k_mark<<<grid, kThreads>>>(v, b->d_chi, nwords, b->d_bits, cnt);
+    k_scan_sums<<<(unsigned)std::max<int64_t>(1, nchunks), kThreads>>>(cnt, nwords, sums);
+    k_scan_serial<<<1, 1>>>(sums, nchunks);
+    k_scan_apply<<<(unsigned)std::max<int64_t>(1, nchunks), kThreads>>>(cnt, nwords, sums, b->d_cum);
+    e = cudaGetLastError();
+    int64_t total = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&total, sums + nchunks, sizeof total, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_cum + nwords, &total, sizeof total, cudaMemcpyHostToDevice);
+    cudaFree(cnt);
+    cudaFree(sums);
+    if (e != cudaSuccess) return cuda_status(e, "symmetric basis build");
+    b->dim = total;
+    XD_CUDA(cudaMalloc((void **)&b->d_reps, std::max<int64_t>(1, total) * sizeof(uint64_t)));
+    XD_CUDA(cudaMalloc((void **)&b->d_stab, std::max<int64_t>(1, total)));
+    v = b->symview();
+    k_compact<<<grid, kThreads>>>(v, nwords, b->d_bits, b->d_cum, b->d_reps, b->d_stab);
+    XD_CUDA(cudaGetLastError());
+    XD_CUDA(cudaDeviceSynchronize());
+    return XD_OK;
+}
+
+// Per-Hamiltonian tables: sqrt(a/m) for a, m in [1, G] and the orbit id of
+// every bond under the group (bilinear forms are averaged over bond orbits).
+xd_status sym_ham_tables(xd_ham_s *h) {
+    const xd_basis_s *b = h->b;
+    const int G = b->G, nb = b->nb;
+    const size_t nsq = (size_t)(G + 1) * (G + 1);
+    std::vector<double> tab(nsq + (nb + 1) / 2 + 1, 0.0);
+    for (int a = 1; a <= G; ++a)
+        for (int m = 1; m <= G; ++m) tab[a * (G + 1) + m] = sqrt((double)a / (double)m);
+    std::vector<int32_t> orb(nb, -1);
+    int norb = 0;
+    for (int q = 0; q < nb; ++q) {
+        if (orb[q] >= 0) continue;
+        for (int g = 0; g < G; ++g) {
+            int a = b->perms[(size_t)g * b->N + b->bonds[q].i];
+            int c = b->perms[(size_t)g * b->N + b->bonds[q].j];
+            for (int p = 0; p < nb; ++p)
+                if (orb[p] < 0 && ((b->bonds[p].i == a && b->bonds[p].j == c) ||
+                                   (b->bonds[p].i == c && b->bonds[p].j == a)))
+                    orb[p] = norb;
+        }
+        ++norb;
+    }
+    memcpy(tab.data() + nsq, orb.data(), nb * sizeof(int32_t));
+    XD_CUDA(cudaMalloc((void **)&h->d_symtab, tab.size() * sizeof(double)));
+    XD_CUDA(cudaMemcpy(h->d_symtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return XD_OK;
+}
+
+struct SymWork {
+    const double *sq;
+    const int32_t *orbit;
+    double *part;
+};
+
+static xd_status sym_work(const xd_ham_s *h, int grid, SymWork *w) {
+    const xd_basis_s *b = h->b;
+    const size_t nsq = (size_t)(b->G + 1) * (b->G + 1);
+    w->sq = h->d_symtab;
+    w->orbit = (const int32_t *)(h->d_symtab + nsq);
+    w->part = nullptr;
+    if (grid > 0) {
+        XD_TRY(ensure_partials(const_cast<xd_ham_s *>(h), (size_t)grid * b->nb * sizeof(double)));
+        w->part = h->d_part;
+    }
+    return XD_OK;
+}
+
+xd_status sym_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, cudaStream_t st) {
+    const xd_basis_s *b = h->b;
+    const int nb = b->nb, G = b->G;
+    SymWork w;
+    XD_TRY(sym_work(h, 0, &w));
+    const SymView v = b->symview();
+    size_t smem = (size_t)nb * 16 + 2 * G * sizeof(double) + (size_t)(G + 1) * (G + 1) * sizeof(double);
+    int grid = grid_for(v.dim, kThreads, 8);
+    if (dt == XD_C128) {
+        auto kern = k_sym_apply<true>;
+        XD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<grid, kThreads, smem, st>>>(v, h->d_bond, nb, b->d_chi, w.sq, (const double2 *)x,
+                                          (double2 *)y);
+    } else {
+        auto kern = k_sym_apply<false>;
+        XD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<grid, kThreads, smem, st>>>(v, h->d_bond, nb, b->d_chi, w.sq, (const double *)x,
+                                          (double *)y);
+    }
+    XD_CUDA(cudaGetLastError());
+    return XD_OK;
+}
+
+xd_status sym_bilinear(const xd_ham_s *h, const void *g, const void *x, xd_dtype dt, double *dJ,
+                       cudaStream_t st) {
+    const xd_basis_s *b = h->b;
+    const int nb = b->nb;
+    const SymView v = b->symview();
+    const int grid = grid_for(v.dim, kThreads, 4);
+    SymWork w;
+    XD_TRY(sym_work(h, grid, &w));
+    const uint64_t *masks = (const uint64_t *)(h->d_bond + nb);
+    for (int b0 = 0; b0 < nb; b0 += kChunk) {
+        if (dt == XD_C128)
+            k_sym_bilinear<true><<<grid, kThreads, 0, st>>>(v, masks, nb, b0, b->d_chi, w.sq,
+                                                            (const double2 *)g, (const double2 *)x,
+                                                            w.part);
+        else
+            k_sym_bilinear<false><<<grid, kThreads, 0, st>>>(v, masks, nb, b0, b->d_chi, w.sq,
+                                                             (const double *)g, (const double *)x,
+                                                             w.part);
+        XD_CUDA(cudaGetLastError());
+    }
+    k_orbit_mean<<<(nb + 127) / 128, 128, 0, st>>>(w.part, grid, nb, w.orbit, dJ);
+    XD_CUDA(cudaGetLastError());
+    return XD_OK;
+}
+
+}  // namespace xd

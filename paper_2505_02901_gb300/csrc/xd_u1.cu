@@ -1,0 +1,243 @@
+// xd_u1.cu -- y = H x and per-bond bilinear forms on U(1) blocks.
+//
+// Pull form (the "apply" of Sec. 3.5 with the vector fill of Sec. 5.1):
+// every row r of y is written once, no atomics.  For row r with state s
+// (a1: unranked from the two-table layout, Sec. 5.2) and every bond b:
+//   a2  equal spins:     +J_b/4 x_r on the diagonal
+//   a3  opposite spins:  -J_b/4 x_r and +J_b/2 x_c, c = index(s ^ m_b)
+//   a4  c from the prefix/postfix tables: c = hi_off[s'>>L] + lo_rank[s'&mask]
+//   a5  gather x_c and accumulate.
+// The diagonal is written as J_sum/4 - sum over flipped bonds of J_b/2.
+
+#include "xd_internal.cuh"
+
+namespace xd {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// largest h in [lo, hi] with hi_off[h] <= r (hi_off is non-decreasing)
+__device__ __forceinline__ uint64_t find_block(const int64_t *__restrict__ hi_off, uint64_t lo,
+                                               uint64_t hi, int64_t r) {
+    while (lo < hi) {
+        uint64_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(hi_off + mid) <= r) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Row r -> (state, block).  The CTA first brackets the blocks of its rows.
+struct RowState {
+    uint64_t s;
+    bool valid;
+};
+
+__device__ __forceinline__ RowState unrank_tile(const U1View &u, int64_t base, int64_t r,
+                                                uint64_t *sh_range) {
+    // sh_range[0..1]: block range of rows [base, base + blockDim.x)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t nh = 1ull << u.P;
+        int64_t last = min(base + (int64_t)blockDim.x, u.dim) - 1;
+        uint64_t h0 = find_block(u.hi_off, 0, nh - 1, base);
+        uint64_t h1 = find_block(u.hi_off, h0, nh - 1, last);
+        sh_range[0] = h0;
+        sh_range[1] = h1;
+    }
+    __syncthreads();
+    RowState rs;
+    rs.valid = r < u.dim;
+    rs.s = 0;
+    if (rs.valid) {
+        uint64_t h = find_block(u.hi_off, sh_range[0], sh_range[1], r);
+        int64_t i = r - __ldg(u.hi_off + h);
+        int m = u.nup - __popcll(h);
+        uint32_t l = __ldg(u.lo_list + __ldg(u.lo_off + m) + (uint32_t)i);
+        rs.s = (h << u.L) | l;
+    }
+    return rs;
+}
+
+__device__ __forceinline__ int64_t rank_of(const U1View &u, uint64_t t) {
+    return __ldg(u.hi_off + (t >> u.L)) + (int64_t)__ldg(u.lo_rank + (t & u.lomask));
+}
+
+template <typename T, int NV>
+struct Vec {
+    T v[NV];
+};
+
+template <typename T, int NV>
+__device__ __forceinline__ void load_row(const T *__restrict__ x, int64_t c, T (&out)[NV]) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = __ldg(x + c * NV + k);
+}
+
+// y = H x.  Bond masks and coefficients J_b/2 are staged in shared memory
+// from the handle's bond table [J (nb) | masks (nb) | sum J / 4].
+template <typename T, int NV>
+__global__ void __launch_bounds__(kThreads) k_apply(U1View u, const double *__restrict__ bond,
+                                                    int nb, const T *__restrict__ x,
+                                                    T *__restrict__ y) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *sm_mask = (uint64_t *)smem;
+    T *sm_half = (T *)(sm_mask + nb);
+    __shared__ uint64_t sh_range[2];
+    const uint64_t *masks = (const uint64_t *)(bond + nb);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        sm_half[b] = (T)(0.5 * bond[b]);
+        sm_mask[b] = masks[b];
+    }
+    const T jq = (T)bond[2 * nb];
+    __syncthreads();
+
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < u.dim;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = base + threadIdx.x;
+        RowState rs = unrank_tile(u, base, r, sh_range);
+        if (!rs.valid) continue;
+        const uint64_t s = rs.s;
+        T acc[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = T(0);
+        T dsub = T(0);
+        for (int b = 0; b < nb; ++b) {
+            const uint64_t mk = sm_mask[b];
+            const uint64_t t = s & mk;
+            if (t != 0 && t != mk) {
+                const int64_t c = rank_of(u, s ^ mk);
+                const T cf = sm_half[b];
+                T xv[NV];
+                load_row<T, NV>(x, c, xv);
+#pragma unroll
+                for (int k = 0; k < NV; ++k) acc[k] += cf * xv[k];
+                dsub += cf;
+            }
+        }
+        T xr[NV];
+        load_row<T, NV>(x, r, xr);
+        const T d = jq - dsub;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) y[r * NV + k] = d * xr[k] + acc[k];
+    }
+}
+
+// Per-bond bilinear forms: part[cta][b] = sum over the CTA's rows of
+// g_r (S_i.S_j x)_r; each warp reduces its lanes with shuffles into its own
+// shared row, the CTA sums its warps in order.  Bonds in chunks of kChunk.
+constexpr int kChunk = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_bilinear(U1View u, const uint64_t *__restrict__ masks,
+                                                       int nb, int b0, const T *__restrict__ g,
+                                                       const T *__restrict__ x,
+                                                       double *__restrict__ part) {
+    __shared__ double acc[kThreads / 32][kChunk];
+    __shared__ uint64_t sh_range[2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nbc = min(kChunk, nb - b0);
+    for (int b = lane; b < nbc; b += 32) acc[warp][b] = 0.0;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < u.dim;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = base + threadIdx.x;
+        RowState rs = unrank_tile(u, base, r, sh_range);
+        double gr = 0.0, xr = 0.0;
+        if (rs.valid) {
+            gr = (double)g[r];
+            xr = (double)x[r];
+        }
+        for (int b = 0; b < nbc; ++b) {
+            double v = 0.0;
+            if (rs.valid) {
+                const uint64_t mk = masks[b0 + b];
+                const uint64_t t = rs.s & mk;
+                if (t != 0 && t != mk) {
+                    const int64_t c = rank_of(u, rs.s ^ mk);
+                    v = gr * (0.5 * (double)x[c] - 0.25 * xr);
+                } else {
+                    v = 0.25 * gr * xr;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) acc[warp][b] += v;
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbc; b += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) s += acc[w][b];
+        part[(size_t)blockIdx.x * nb + b0 + b] = s;
+    }
+}
+
+// out[b] = sum_c part[c][b] in fixed order.
+__global__ void k_sum_columns(const double *__restrict__ part, int rows, int cols,
+                              double *__restrict__ out) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= cols) return;
+    double s = 0.0;
+    for (int c = 0; c < rows; ++c) s += part[(size_t)c * cols + b];
+    out[b] = s;
+}
+
+}  // namespace
+
+template <typename T, int NV>
+static xd_status launch_apply(const xd_ham_s *h, const void *x, void *y, cudaStream_t st) {
+    const double *bondbuf = h->d_bond;
+    const U1View u = h->b->u1view();
+    const int nb = h->b->nb;
+    size_t smem = (size_t)nb * (sizeof(uint64_t) + sizeof(T));
+    auto kern = k_apply<T, NV>;
+    if (smem > 48 * 1024) XD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int grid = grid_for(u.dim, kThreads, 8);
+    kern<<<grid, kThreads, smem, st>>>(u, bondbuf, nb, (const T *)x, (T *)y);
+    XD_CUDA(cudaGetLastError());
+    return XD_OK;
+}
+
+xd_status u1_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, int nvec,
+                   cudaStream_t st) {
+    if (dt == XD_F64) {
+        switch (nvec) {
+            case 1: return launch_apply<double, 1>(h, x, y, st);
+            case 2: return launch_apply<double, 2>(h, x, y, st);
+            case 4: return launch_apply<double, 4>(h, x, y, st);
+            default: return launch_apply<double, 8>(h, x, y, st);
+        }
+    }
+    switch (nvec) {
+        case 1: return launch_apply<float, 1>(h, x, y, st);
+        case 2: return launch_apply<float, 2>(h, x, y, st);
+        case 4: return launch_apply<float, 4>(h, x, y, st);
+        default: return launch_apply<float, 8>(h, x, y, st);
+    }
+}
+
+xd_status u1_bilinear(const xd_ham_s *h, const void *g, const void *x, xd_dtype dt, double *dJ,
+                      cudaStream_t st) {
+    const xd_basis_s *b = h->b;
+    const int nb = b->nb;
+    const U1View u = b->u1view();
+    const int grid = grid_for(u.dim, kThreads, 4);
+    xd_ham_s *hm = const_cast<xd_ham_s *>(h);
+    XD_TRY(ensure_partials(hm, sizeof(double) * (size_t)grid * nb));
+    const uint64_t *d_masks = (const uint64_t *)(h->d_bond + nb);
+    double *d_part = hm->d_part;
+    for (int b0 = 0; b0 < nb; b0 += kChunk) {
+        if (dt == XD_F64)
+            k_bilinear<double><<<grid, kThreads, 0, st>>>(u, d_masks, nb, b0, (const double *)g,
+                                                          (const double *)x, d_part);
+        else
+            k_bilinear<float><<<grid, kThreads, 0, st>>>(u, d_masks, nb, b0, (const float *)g,
+                                                         (const float *)x, d_part);
+        XD_CUDA(cudaGetLastError());
+    }
+    k_sum_columns<<<(nb + 127) / 128, 128, 0, st>>>(d_part, grid, nb, dJ);
+    XD_CUDA(cudaGetLastError());
+    return XD_OK;
+}
+
+}  // namespace xd

@@ -1,0 +1,106 @@
+"""Lanczos (a6, a7), bilinear forms and gradients (a8) against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2505_02901_gb300 import workloads as W
+from tests.gpu_common import api, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def test_chain16_lanczos_f64_and_f32(orc):
+    """C1 workload: periodic N=16 chain, Sz=0, 100 steps."""
+    A = api()
+    N = 16
+    bonds = W.chain(N)
+    st = orc.enumerate_states(N, 8)
+    ham = A.Hamiltonian(A.Basis(N, 8, bonds), np.ones(N))
+    v0 = orc.rng_normal(1, 0, st.size)
+    a, b = orc.lanczos(lambda v: orc.apply_u1(N, st, bonds, np.ones(N), v), st.size, v0, 100)
+    e_ref = orc.tridiag_eigvals(a, b)[0]
+    info = ham.lanczos(max_iter=100, seed=1, storage=torch.float64, nev=3)
+    assert abs(info["evals"][0] - e_ref) <= 1e-10 * abs(e_ref)
+    # the first steps of the recurrence agree with the oracle's
+    assert np.abs(info["alpha"][:10] - a[:10]).max() < 1e-10
+    assert np.abs(info["beta"][:10] - b[:10]).max() < 1e-10
+    info32 = ham.lanczos(max_iter=100, seed=1, storage=torch.float32)
+    assert abs(info32["evals"][0] - e_ref) <= 1e-6 * abs(e_ref)
+
+
+def test_ground_state_vector_and_residual(orc):
+    A = api()
+    N = 14
+    bonds = W.random_bonds(N, 24, 3)
+    J = W.uniform_couplings(24, 4)
+    st = orc.enumerate_states(N, 7)
+    w, V = np.linalg.eigh(orc.dense_u1(N, st, bonds, J))
+    ham = A.Hamiltonian(A.Basis(N, 7, bonds), J)
+    e0, psi, info = ham.ground_state(max_iter=150, seed=3)
+    assert abs(e0 - w[0]) <= 1e-10 * abs(w[0])
+    p = psi.cpu().numpy()
+    assert abs(np.linalg.norm(p) - 1) < 1e-12
+    assert abs(abs(p @ V[:, 0]) - 1) < 1e-8
+    assert info["resid"][0] < 1e-6
+
+
+def test_bilinear_matches_oracle(orc):
+    A = api()
+    for N, nup, seed in [(10, 5, 1), (13, 6, 2), (16, 8, 3)]:
+        bonds = W.random_bonds(N, 2 * N, seed)
+        J = W.uniform_couplings(2 * N, seed)
+        st = orc.enumerate_states(N, nup)
+        ham = A.Hamiltonian(A.Basis(N, nup, bonds), J)
+        g, x = orc.rng_normal(seed, 0, st.size), orc.rng_normal(seed + 9, 0, st.size)
+        dJ = ham.bilinear(torch.from_numpy(g).cuda(), torch.from_numpy(x).cuda()).cpu().numpy()
+        ref = orc.bond_forms(N, st, bonds, g, x)
+        assert rel_l2(dJ, ref) <= 1e-12
+        # deterministic: same call, same bits
+        dJ2 = ham.bilinear(torch.from_numpy(g).cuda(), torch.from_numpy(x).cuda()).cpu().numpy()
+        assert np.array_equal(dJ, dJ2)
+
+
+def test_autograd_apply(orc):
+    A = api()
+    N, nup = 12, 6
+    bonds = W.ladder(6, 2)
+    J = W.uniform_couplings(24, 8)
+    st = orc.enumerate_states(N, nup)
+    ham = A.Hamiltonian(A.Basis(N, nup, bonds), J)
+    Jt = torch.tensor(J, dtype=torch.float64, device="cuda", requires_grad=True)
+    x = torch.from_numpy(orc.rng_normal(4, 0, st.size)).cuda().requires_grad_(True)
+    c = torch.from_numpy(orc.rng_normal(5, 0, st.size)).cuda()
+    loss = (c * A.heisenberg_apply(ham, Jt, x)).sum()
+    loss.backward()
+    ref_J = orc.bond_forms(N, st, bonds, c.cpu().numpy(), x.detach().cpu().numpy())
+    ref_x = orc.apply_u1(N, st, bonds, J, c.cpu().numpy())
+    assert rel_l2(Jt.grad.cpu().numpy(), ref_J) <= 1e-12
+    assert rel_l2(x.grad.cpu().numpy(), ref_x) <= 1e-12
+
+
+def test_energy_gradient_ladder(orc):
+    """C3 pattern at oracle size: ladder with duplicated rungs, dE0/dJ by the
+    backward kernel vs central finite differences and Hellmann-Feynman."""
+    A = api()
+    L = 6
+    bonds = W.ladder(L, 2)
+    N = 2 * L
+    J = W.uniform_couplings(bonds.shape[0], 3)
+    st = orc.enumerate_states(N, L)
+    ham = A.Hamiltonian(A.Basis(N, L, bonds), J)
+    Jt = torch.tensor(J, dtype=torch.float64, device="cuda", requires_grad=True)
+    E = A.ground_energy(ham, Jt, max_iter=200, seed=3)
+    E.backward()
+    g = Jt.grad.cpu().numpy()
+    w, V = np.linalg.eigh(orc.dense_u1(N, st, bonds, J))
+    hf = orc.bond_forms(N, st, bonds, V[:, 0], V[:, 0])
+    assert abs(E.item() - w[0]) < 1e-10 * abs(w[0])
+    assert np.abs(g - hf).max() < 1e-8
+    h = 1e-5
+    for b in (0, 3, 2 * L, 3 * L):
+        e = np.zeros_like(J); e[b] = h
+        fd = (np.linalg.eigvalsh(orc.dense_u1(N, st, bonds, J + e))[0]
+              - np.linalg.eigvalsh(orc.dense_u1(N, st, bonds, J - e))[0]) / (2 * h)
+        assert abs(fd - g[b]) < 1e-6
+    assert abs(J @ g - w[0]) < 1e-9
+    assert np.abs(g[2 * L:3 * L] - g[3 * L:]).max() < 1e-9
