@@ -205,6 +205,7 @@ static xd_status check_group(const xd_basis_s *b) {
 }
 
 static void free_basis(xd_basis_s *b) {
+    block_layout_free(b);
     cudaFree(b->d_hi_off);
     cudaFree(b->d_lo_rank);
     cudaFree(b->d_lo_list);
@@ -315,6 +316,7 @@ xd_status xd_basis_create(int N, int nup, const int32_t *bonds, int nb, const xd
     }
     xd_status s = build_u1(b);
     if (s == XD_OK && b->sym) s = sym_build(b);
+    if (s == XD_OK && block_layout_wanted(b)) s = block_layout_build(b);
     if (s != XD_OK) {
         free_basis(b);
         return s;
@@ -423,6 +425,7 @@ static xd_status set_J(xd_ham_s *h, const double *J) {
     buf[2 * b->nb] = 0.25 * q;
     XD_CUDA(cudaMemcpy(h->d_bond, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice));
     if (b->sym && !h->d_symtab) XD_TRY(sym_ham_tables(h));
+    if (b->blk.ok) XD_TRY(block_ham_tables(h));
     return XD_OK;
 }
 
@@ -467,6 +470,7 @@ void xd_ham_destroy(xd_ham h) {
     cudaFree(h->d_bond);
     cudaFree(h->d_lzpart);
     cudaFree(h->d_symtab);
+    cudaFree(h->d_dpost);
     cudaFree(h->d_part);
     cudaFree(h->d_scal);
     delete h;

@@ -70,6 +70,21 @@ struct Bond {
     int i, j;
 };
 
+// Block-structured layout of a large U(1) block (xd_u1_block.cu).
+struct BlockLayoutHost {
+    bool ok = false;
+    int w = 8;                    // low part width of the two-level in-class rank
+    int npre = 0, ncross = 0;
+    int64_t nblk = 0;             // non-empty prefix blocks
+    int maxblk = 0;               // largest block, C(L, L/2)
+    std::vector<int> post;        // postfix bond ids
+    uint32_t *d_order = nullptr;  // prefixes, largest block first
+    uint32_t *d_csr_off = nullptr, *d_csr = nullptr;
+    uint16_t *d_off2 = nullptr;
+    uint8_t *d_rank8 = nullptr;
+    int32_t *d_pre = nullptr, *d_cross = nullptr;
+};
+
 }  // namespace xd
 
 struct xd_basis_s {
@@ -95,6 +110,7 @@ struct xd_basis_s {
     uint64_t *d_act = nullptr;
     int nchunk = 0;
     double *d_chi = nullptr;  // [G][2]
+    xd::BlockLayoutHost blk;
 
     xd::U1View u1view() const;
     xd::SymView symview() const;
@@ -111,6 +127,7 @@ struct xd_ham_s {
     double *d_lzpart = nullptr;     // Lanczos reduction partials
     int lzpart_n = 0;
     double *d_symtab = nullptr;     // symmetric blocks: sqrt ratios [(G+1)^2] | bond orbit ids
+    double *d_dpost = nullptr;      // block layout: postfix diagonal per L-bit word
 };
 
 namespace xd {
@@ -131,6 +148,12 @@ xd_status sym_bilinear(const xd_ham_s *h, const void *g, const void *x,
 // vector kernels (xd_vec.cu)
 xd_status vec_random(int64_t n, uint64_t seed, void *out, xd_dtype dt,
                      cudaStream_t st);
+// block-structured U(1) product (xd_u1_block.cu)
+bool block_layout_wanted(const xd_basis_s *b);
+xd_status block_layout_build(xd_basis_s *b);
+void block_layout_free(xd_basis_s *b);
+xd_status block_ham_tables(xd_ham_s *h);
+xd_status block_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, cudaStream_t st);
 // forget cached batch plans that use this handle (xd_batch.cu)
 void batch_forget(const xd_ham_s *h);
 // workspace helper

@@ -200,6 +200,7 @@ static xd_status launch_apply(const xd_ham_s *h, const void *x, void *y, cudaStr
 
 xd_status u1_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, int nvec,
                    cudaStream_t st) {
+    if (nvec == 1 && h->b->blk.ok) return block_apply(h, x, y, dt, st);
     if (dt == XD_F64) {
         switch (nvec) {
             case 1: return launch_apply<double, 1>(h, x, y, st);

@@ -67,17 +67,19 @@ def test_sym_lanczos_spectra_union(orc):
 
 
 def test_sym_gradient_matches_u1(orc):
+    """Chain N=12 (N/2 even: the ground state has momentum 0)."""
     A = api()
-    N = 10
+    N = 12
     bonds = W.chain(N)
     J = np.ones(N)
-    basis = A.Basis(N, 5, bonds, symmetry=(W.chain_translations(N), W.chain_characters(N, 0)))
+    basis = A.Basis(N, 6, bonds, symmetry=(W.chain_translations(N), W.chain_characters(N, 0)))
     ham = A.Hamiltonian(basis, J)
     e0, psi, _ = ham.ground_state(max_iter=100, seed=1)
     g = ham.energy_grad(psi)
-    st = orc.enumerate_states(N, 5)
+    st = orc.enumerate_states(N, 6)
     w, V = np.linalg.eigh(orc.dense_u1(N, st, bonds, J))
     hf = orc.bond_forms(N, st, bonds, V[:, 0], V[:, 0])
+    assert w[1] - w[0] > 1e-6
     assert abs(e0 - w[0]) < 1e-10 * abs(w[0])
     assert np.abs(g - hf).max() < 1e-8
 

@@ -24,6 +24,13 @@ def _cases():
     b, J = W.square_j1j2(4, 4)
     out.append((16, 8, b, J))
     out.append((20, 10, W.ladder(10, 2), W.uniform_couplings(40, 3)))
+    # block-structured path (N >= 20): irregular graphs mixing prefix,
+    # postfix and cross bonds, ragged block sizes (nup != N/2)
+    out.append((21, 7, W.random_bonds(21, 42, 21), W.uniform_couplings(42, 21, -1.0, 1.0)))
+    out.append((22, 11, W.random_bonds(22, 60, 22), W.uniform_couplings(60, 22)))
+    b, J = W.square_j1j2(4, 6)
+    out.append((24, 12, b, J))
+    out.append((24, 9, W.random_bonds(24, 30, 24), W.uniform_couplings(30, 24)))
     return out
 
 
@@ -45,7 +52,7 @@ def test_apply_f64_matches_oracle(orc, case):
     assert np.abs(y - yo).max() <= 1e-12 * np.abs(yo).max()
 
 
-@pytest.mark.parametrize("case", [3, 6, 9, 12, 13, 14])
+@pytest.mark.parametrize("case", [3, 6, 9, 12, 13, 14, 16, 17])
 @pytest.mark.parametrize("nvec", [1, 2, 4, 8])
 def test_apply_f32_and_multi_rhs(orc, case, nvec):
     A = api()
