@@ -73,16 +73,16 @@ struct Bond {
 // Block-structured layout of a large U(1) block (xd_u1_block.cu).
 struct BlockLayoutHost {
     bool ok = false;
-    int w = 8;                    // low part width of the two-level in-class rank
-    int npre = 0, ncross = 0;
+    int npre = 0, ncross = 0, npost = 0, npost_pad = 0;
     int64_t nblk = 0;             // non-empty prefix blocks
     int maxblk = 0;               // largest block, C(L, L/2)
     std::vector<int> post;        // postfix bond ids
-    uint32_t *d_order = nullptr;  // prefixes, largest block first
-    uint32_t *d_csr_off = nullptr, *d_csr = nullptr;
-    uint16_t *d_off2 = nullptr;
-    uint8_t *d_rank8 = nullptr;
-    int32_t *d_pre = nullptr, *d_cross = nullptr;
+    uint32_t *d_order = nullptr;  // non-empty prefixes, ascending
+    uint16_t *d_ptab = nullptr;   // postfix flip targets, bond-major
+    uint16_t *d_xtab = nullptr;   // cross flip targets per postfix site
+    int32_t *d_postid = nullptr;
+    int32_t *d_pre = nullptr, *d_cross = nullptr, *d_csite = nullptr;
+    int ncsite = 0;
 };
 
 }  // namespace xd

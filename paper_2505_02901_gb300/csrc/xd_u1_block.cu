@@ -6,18 +6,24 @@
 // owns one prefix block h (the C(L, m) consecutive rows sharing the prefix,
 // m = nup - popcount(h)) and the bonds fall into three kinds:
 //   postfix bonds (both sites < L): the flipped state stays in block h; its
-//       rank inside the block comes from a per-postfix-state neighbour list
-//       (CSR of (rank, bond) for every L-bit word) and x of the whole block
-//       is staged in shared memory, so these gathers are shared-memory loads;
+//       rank inside the block comes from a bond-major target table indexed by
+//       the in-class rank of the row (so a warp reads consecutive entries),
+//       and x of the whole block is staged in shared memory, so these
+//       gathers are shared-memory loads;
 //   prefix bonds (both sites >= L): the flip maps block h to block h ^ m_b
 //       with the same in-block rank, so row i reads x[off(h') + i]: one
 //       coalesced stream per active bond, decided once per block;
-//   cross bonds (one site each side): the flip changes the prefix bit (one
-//       neighbour block per bond, decided once per block) and one postfix
-//       bit of l; the in-class rank of the new postfix word comes from two
-//       small shared tables (high part offsets, low part ranks).
-// The diagonal is d_pre(h) + d_post(l) + the cross-bond terms.  Blocks are
-// processed largest first (static round robin over the size-sorted list).
+//   cross bonds (one site each side): the flip changes the prefix bit a (one
+//       neighbour block per prefix site a) and one postfix bit j of l.  The
+//       neighbour block of each cross site is copied into shared memory with
+//       cp.async (double buffered: the copy of the next neighbour overlaps
+//       the gathers from the current one); the rank of l ^ 2^j in its class
+//       comes from a per-site table indexed by the row's in-class rank.
+// Each thread owns K rows of the block (i = tid + k * 1024) and keeps their
+// accumulators in registers across the three phases.  The diagonal is
+// d_pre(h) + d_post(l) + the cross-bond terms.  Prefix blocks are walked in
+// ascending order (static round robin), so the blocks reached by flips on
+// low prefix bits are still in L2.
 
 #include <algorithm>
 #include <vector>
@@ -28,87 +34,116 @@ namespace xd {
 
 namespace {
 
+template <typename T>
 struct PreEnt {
-    int64_t off;
-    double coef;
-};
-struct CrossEnt {
-    int64_t off;   // first row of the neighbour block
-    double coef;   // J/2
-    int j;         // postfix site
-    int req;       // value of bit j that makes the bond flip
-    int mcls;      // class (postfix popcount) of the flipped postfix word
-    int pad;
+    const T *src;   // x + first row of the neighbour block
+    T coef;         // J/2
 };
 
 struct BlkParams {
     U1View u;
-    const uint32_t *order;
+    const uint32_t *order;  // non-empty prefixes, ascending
     int64_t nblk;
-    const uint32_t *csr_off;
-    const uint32_t *csr;
-    const uint16_t *off2;  // [(L+1)][2^(L-w)]
-    const uint8_t *rank8;  // [2^w]
-    int w;
-    const double *dpost;   // [2^L]
-    const double *J;       // [nb]
-    const int32_t *pre;    // [npre][3]: prefix bit a, prefix bit b, bond id
+    const uint16_t *ptab;   // [npost_pad][2^L]: rank of l ^ m_b in class, maxblk = no flip
+    const uint16_t *xtab;   // [nslot][2^L]: rank of l ^ 2^j_slot in its class
+    const double *dpost;    // [2^L]: postfix diagonal, by class-ordered position
+    const int32_t *post;    // [npost] bond ids
+    int npost, npost_pad;   // postfix bonds, padded to a multiple of 8 (dummy rows never flip)
+    const double *J;        // [nb]
+    const int32_t *pre;     // [npre][3]: prefix bit a, prefix bit b, bond id
     int npre;
-    const int32_t *cross;  // [ncross][3]: prefix bit, postfix site, bond id
+    const int32_t *cross;   // [ncross][4]: prefix bit, postfix site, bond id, slot (grouped by prefix bit)
     int ncross;
+    const int32_t *csite;   // [ncsite][3]: prefix bit a, first cross bond, end cross bond
+    int ncsite;
     int nb;
     int maxblk;
+    double jcross;          // sum over cross bonds of J/4
+};
+
+constexpr int kBT = 1024;   // threads per CTA
+
+template <int L>
+struct Geo {
+    static constexpr uint32_t nlo = 1u << L;
+    static constexpr int maxblk = L == 16 ? 12870 : L == 15 ? 6435 : L == 14 ? 3432 : L == 13 ? 1716
+                                : L == 12 ? 924 : L == 11 ? 462 : 252;
+    static constexpr int K = (maxblk + kBT - 1) / kBT;  // rows per thread
 };
 
 template <typename T>
 struct SmemLayout {
-    size_t xs, off2, rank8, coef, pre, cross, total;
-    __host__ __device__ SmemLayout(const BlkParams &p) {
+    size_t xs, nbuf, pc, cc, cmeta, pre, site, total;
+    __host__ __device__ SmemLayout(const BlkParams &p, int nbufs) {
         size_t o = 0;
         auto al = [&](size_t a) { o = (o + a - 1) / a * a; };
         xs = o;
-        o += (size_t)p.maxblk * sizeof(T);
+        o += (size_t)(p.maxblk + 1) * sizeof(T);  // + a zero slot for "no flip"
         al(16);
-        off2 = o;
-        o += (size_t)(p.u.L + 1) * (1u << (p.u.L - p.w)) * sizeof(uint16_t);
+        nbuf = o;
+        o += (size_t)nbufs * p.maxblk * sizeof(T);
         al(16);
-        rank8 = o;
-        o += (size_t)(1u << p.w);
+        pc = o;
+        o += (size_t)p.npost_pad * sizeof(T);
         al(16);
-        coef = o;
-        o += (size_t)p.nb * sizeof(T);
+        cc = o;
+        o += (size_t)p.ncross * sizeof(T);
+        al(16);
+        cmeta = o;
+        o += (size_t)p.ncross * sizeof(uint32_t);
         al(16);
         pre = o;
-        o += (size_t)p.npre * sizeof(PreEnt);
+        o += (size_t)p.npre * sizeof(PreEnt<T>);
         al(16);
-        cross = o;
-        o += (size_t)p.ncross * sizeof(CrossEnt);
+        site = o;
+        o += (size_t)p.ncsite * sizeof(int64_t) * 2;
         al(16);
         total = o;
     }
 };
 
+__device__ __forceinline__ void cp_async(void *smem_dst, const void *gsrc, int bytes) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_block_apply(BlkParams p, const T *__restrict__ x,
+__device__ __forceinline__ void stage(T *dst, const T *src, int n) {
+    for (int i = threadIdx.x; i < n; i += kBT) cp_async(dst + i, src + i, (int)sizeof(T));
+    cp_commit();
+}
+
+template <typename T, int L, int NBUF>
+__global__ void __launch_bounds__(kBT) k_block_apply(BlkParams p, const T *__restrict__ x,
                                                      T *__restrict__ y) {
+    using G = Geo<L>;
+    constexpr uint32_t nlo = G::nlo;
+    constexpr int K = G::K;
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmemLayout<T> lay(p);
+    const SmemLayout<T> lay(p, NBUF);
     T *xs = (T *)(smem + lay.xs);
-    uint16_t *off2 = (uint16_t *)(smem + lay.off2);
-    uint8_t *rank8 = (uint8_t *)(smem + lay.rank8);
-    T *coef = (T *)(smem + lay.coef);
-    PreEnt *pl = (PreEnt *)(smem + lay.pre);
-    CrossEnt *cl = (CrossEnt *)(smem + lay.cross);
+    T *nbuf = (T *)(smem + lay.nbuf);
+    T *pc = (T *)(smem + lay.pc);
+    T *cc = (T *)(smem + lay.cc);
+    uint32_t *cmeta = (uint32_t *)(smem + lay.cmeta);
+    PreEnt<T> *pl = (PreEnt<T> *)(smem + lay.pre);
+    int64_t *site = (int64_t *)(smem + lay.site);  // [ncsite][2]: neighbour offset, (n << 1) | req
     __shared__ int sh_npa;
     __shared__ double sh_dpre;
 
     const U1View &u = p.u;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int hw = u.L - p.w;
-    for (int k = tid; k < (u.L + 1) << hw; k += blockDim.x) off2[k] = p.off2[k];
-    for (int k = tid; k < (1 << p.w); k += blockDim.x) rank8[k] = p.rank8[k];
-    for (int k = tid; k < p.nb; k += blockDim.x) coef[k] = (T)(0.5 * p.J[k]);
-    const uint32_t wmask = (1u << p.w) - 1;
+    for (int k = tid; k < p.npost_pad; k += kBT) pc[k] = k < p.npost ? (T)(0.5 * p.J[p.post[k]]) : T(0);
+    for (int q = tid; q < p.ncross; q += kBT) {
+        cc[q] = (T)(0.5 * p.J[p.cross[4 * q + 2]]);
+        cmeta[q] = (uint32_t)p.cross[4 * q + 1] | ((uint32_t)p.cross[4 * q + 3] << 8);
+    }
 
     for (int64_t t = blockIdx.x; t < p.nblk; t += gridDim.x) {
         const uint64_t h = p.order[t];
@@ -117,7 +152,8 @@ __global__ void __launch_bounds__(256) k_block_apply(BlkParams p, const T *__res
         const int n = (int)(__ldg(u.lo_off + m + 1) - l0);
         const int64_t off = __ldg(u.hi_off + h);
         __syncthreads();  // previous block done with shared memory
-        for (int i = tid; i < n; i += blockDim.x) xs[i] = x[off + i];
+        stage(xs, x + off, n);
+        if (tid == 0) xs[p.maxblk] = T(0);
         if (warp == 0) {
             // active prefix bonds (ballot compaction) and the prefix diagonal
             int cnt = 0;
@@ -137,59 +173,127 @@ __global__ void __launch_bounds__(256) k_block_apply(BlkParams p, const T *__res
                 const unsigned bal = __ballot_sync(0xffffffffu, act);
                 if (act) {
                     const int pos = cnt + __popc(bal & ((1u << lane) - 1));
-                    pl[pos].off = __ldg(u.hi_off + (h ^ ((1ull << a) | (1ull << b))));
-                    pl[pos].coef = 0.5 * Jq;
+                    PreEnt<T> e;
+                    e.src = x + __ldg(u.hi_off + (h ^ ((1ull << a) | (1ull << b))));
+                    e.coef = (T)(0.5 * Jq);
+                    pl[pos] = e;
                 }
                 cnt += __popc(bal);
-            }
-            for (int q = lane; q < p.ncross; q += 32) {
-                const int a = p.cross[3 * q], j = p.cross[3 * q + 1];
-                const double Jq = p.J[p.cross[3 * q + 2]];
-                const int hb = (int)((h >> a) & 1);
-                CrossEnt e;
-                e.off = __ldg(u.hi_off + (h ^ (1ull << a)));
-                e.coef = 0.5 * Jq;
-                e.j = j;
-                e.req = 1 - hb;
-                e.mcls = hb ? m + 1 : m - 1;
-                e.pad = 0;
-                cl[q] = e;
-                dpre += 0.25 * Jq;  // cross bonds start at +J/4; flips subtract J/2
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) dpre += __shfl_xor_sync(0xffffffffu, dpre, o);
             if (lane == 0) {
                 sh_npa = cnt;
-                sh_dpre = dpre;
+                sh_dpre = dpre + p.jcross;
+            }
+        } else if (warp == 1) {
+            for (int c = lane; c < p.ncsite; c += 32) {
+                const int a = p.csite[3 * c];
+                const int hb = (int)((h >> a) & 1);
+                const int mn = hb ? m + 1 : m - 1;  // class of the neighbour block
+                const int nn = (mn >= 0 && mn <= L) ? (int)(__ldg(u.lo_off + mn + 1) - __ldg(u.lo_off + mn)) : 0;
+                site[2 * c] = __ldg(u.hi_off + (h ^ (1ull << a)));
+                site[2 * c + 1] = ((int64_t)nn << 1) | (int64_t)(1 - hb);
             }
         }
         __syncthreads();
-        const int npa = sh_npa;
-        const T dpre = (T)sh_dpre;
-        for (int i = tid; i < n; i += blockDim.x) {
-            const uint32_t l = __ldg(u.lo_list + l0 + i);
-            T acc = T(0), dsub = T(0);
-            // postfix bonds: shared-memory gathers inside the block
-            const uint32_t e1 = __ldg(p.csr_off + l + 1);
-            for (uint32_t e = __ldg(p.csr_off + l); e < e1; ++e) {
-                const uint32_t v = __ldg(p.csr + e);
-                acc += coef[v >> 16] * xs[v & 0xffffu];
+        // the first cross neighbour copy overlaps the postfix and prefix phases
+        if (p.ncsite > 0) stage(nbuf, x + site[0], (int)(site[1] >> 1));
+        if (p.ncsite > 0) cp_wait<1>(); else cp_wait<0>();
+        __syncthreads();  // xs complete
+
+        T acc[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] = T(0);
+        // postfix bonds: target ranks from the bond-major table (compile-time
+        // stride; "no flip" points at the zero slot), x from xs, branch free
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int i = tid + k * kBT;
+            if (i < n) {
+                const uint16_t *pt = p.ptab + l0 + i;
+                const T *pcb = pc;
+                T a = T(0);
+#pragma unroll 1
+                for (int b0 = 0; b0 < p.npost_pad; b0 += 8, pt += 8 * nlo, pcb += 8) {
+                    uint32_t r[8];
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) r[v] = __ldg(pt + v * nlo);
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) a += pcb[v] * xs[r[v]];
+                }
+                acc[k] += a;
             }
-            // prefix bonds: coalesced streams from the neighbour blocks
-            for (int q = 0; q < npa; ++q) acc += (T)pl[q].coef * x[pl[q].off + i];
-            // cross bonds
-            for (int q = 0; q < p.ncross; ++q) {
-                const CrossEnt &e = cl[q];
-                if ((int)((l >> e.j) & 1) == e.req) {
-                    const uint32_t l2 = l ^ (1u << e.j);
-                    const int r2 = off2[(e.mcls << hw) + (l2 >> p.w)] + rank8[l2 & wmask];
-                    const T c = (T)e.coef;
-                    acc += c * x[e.off + r2];
-                    dsub += c;
+        }
+        // prefix bonds: coalesced streams from the neighbour blocks
+        {
+            const int npa = sh_npa;
+#pragma unroll 1
+            for (int q = 0; q < npa; ++q) {
+                const PreEnt<T> e = pl[q];
+                T v[K];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const int i = tid + k * kBT;
+                    v[k] = i < n ? __ldg(e.src + i) : T(0);
+                }
+#pragma unroll
+                for (int k = 0; k < K; ++k) acc[k] += e.coef * v[k];
+            }
+        }
+        // cross bonds: one staged neighbour block per prefix site; a flip adds
+        // J/2 (x_target - x_row), which also takes J/2 off the diagonal
+        for (int c = 0; c < p.ncsite; ++c) {
+            T *buf = nbuf + (NBUF == 2 ? (c & 1) : 0) * p.maxblk;
+            if (NBUF == 2) {
+                if (c + 1 < p.ncsite) {
+                    __syncthreads();  // the other buffer is free (its site finished)
+                    stage(nbuf + ((c + 1) & 1) * p.maxblk, x + site[2 * (c + 1)], (int)(site[2 * c + 3] >> 1));
+                    cp_wait<1>();
+                } else {
+                    cp_wait<0>();
+                }
+            } else {
+                if (c > 0) {
+                    __syncthreads();
+                    stage(buf, x + site[2 * c], (int)(site[2 * c + 1] >> 1));
+                }
+                cp_wait<0>();
+            }
+            __syncthreads();  // buffer of site c complete
+            const uint32_t req = (uint32_t)(site[2 * c + 1] & 1);
+            const int q0 = p.csite[3 * c + 1], q1 = p.csite[3 * c + 2];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int i = tid + k * kBT;
+                if (i < n) {
+                    const uint32_t l = __ldg(u.lo_list + l0 + i);
+                    const T xi = xs[i];
+                    T a = T(0);
+#pragma unroll 1
+                    for (int q = q0; q < q1; ++q) {
+                        const uint32_t meta = cmeta[q];
+                        // rank of l ^ 2^j in its class: inside the buffer even
+                        // when the bond does not flip; the select drops that value
+                        const bool f = ((l >> (meta & 31u)) & 1u) == req;
+                        if constexpr (sizeof(T) == 8) {
+                            // double: the FP64 pipe is the scarce one, branch instead
+                            if (f) a += cc[q] * (buf[__ldg(p.xtab + (size_t)(meta >> 8) * nlo + (l0 + i))] - xi);
+                        } else {
+                            const uint32_t r2 = __ldg(p.xtab + (size_t)(meta >> 8) * nlo + (l0 + i));
+                            const T t = cc[q] * (buf[r2] - xi);
+                            a += f ? t : T(0);
+                        }
+                    }
+                    acc[k] += a;
                 }
             }
-            const T d = dpre + (T)__ldg(p.dpost + l) - dsub;
-            y[off + i] = d * xs[i] + acc;
+        }
+        const T dpre = (T)sh_dpre;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int i = tid + k * kBT;
+            if (i < n) y[off + i] = (dpre + (T)__ldg(p.dpost + l0 + i)) * xs[i] + acc[k];
         }
     }
 }
@@ -205,67 +309,79 @@ static int64_t binom_h(int n, int k) {
     return r;
 }
 
-bool block_layout_wanted(const xd_basis_s *b) { return !b->sym && b->N >= 20 && b->L >= 10; }
+bool block_layout_wanted(const xd_basis_s *b) {
+    if (b->sym || b->N < 20 || b->L < 10) return false;
+    int ncross = 0;
+    for (const Bond &bd : b->bonds) {
+        int i = std::min(bd.i, bd.j), j = std::max(bd.i, bd.j);
+        ncross += (i < b->L && j >= b->L);
+    }
+    return ncross <= 1024 && b->L >= 10 && b->L <= 16;
+}
 
 xd_status block_layout_build(xd_basis_s *b) {
-    const int L = b->L, P = b->P, N = b->N, nup = b->nup;
+    const int L = b->L, P = b->P, nup = b->nup;
     BlockLayoutHost &bl = b->blk;
-    bl.w = std::min(8, L);
-    const int hw = L - bl.w;
     // classify bonds
-    std::vector<int32_t> pre, cross;
-    std::vector<int> post;
+    std::vector<int32_t> pre, cross, post;
+    std::vector<int> slot_site;
     for (int k = 0; k < b->nb; ++k) {
         int i = b->bonds[k].i, j = b->bonds[k].j;
         if (i > j) std::swap(i, j);
-        if (j < L) post.push_back(k);
-        else if (i >= L) pre.insert(pre.end(), {i - L, j - L, k});
-        else cross.insert(cross.end(), {j - L, i, k});
-    }
-    bl.npre = (int)pre.size() / 3;
-    bl.ncross = (int)cross.size() / 3;
-    bl.post = post;
-    // CSR of postfix flips for every L-bit word: (rank of the flipped word
-    // inside its popcount class, bond id)
-    const uint32_t nlo = 1u << L;
-    std::vector<uint32_t> off(nlo + 1, 0), ent;
-    ent.reserve((size_t)nlo * post.size() / 2 + 16);
-    for (uint32_t l = 0; l < nlo; ++l) {
-        off[l] = (uint32_t)ent.size();
-        for (int k : post) {
-            int i = b->bonds[k].i, j = b->bonds[k].j;
-            if (((l >> i) & 1) == ((l >> j) & 1)) continue;
-            uint32_t t = l ^ (1u << i) ^ (1u << j);
-            ent.push_back(b->h_lo_rank[t] | ((uint32_t)k << 16));
+        if (j < L) {
+            post.push_back(k);
+        } else if (i >= L) {
+            pre.insert(pre.end(), {i - L, j - L, k});
+        } else {
+            int slot = (int)(std::find(slot_site.begin(), slot_site.end(), i) - slot_site.begin());
+            if (slot == (int)slot_site.size()) slot_site.push_back(i);
+            cross.insert(cross.end(), {j - L, i, k, slot});
         }
     }
-    off[nlo] = (uint32_t)ent.size();
-    // two-level in-class rank tables
-    std::vector<uint16_t> off2((size_t)(L + 1) << hw, 0);
-    for (int mcls = 0; mcls <= L; ++mcls) {
-        uint32_t run = 0;
-        for (uint32_t a = 0; a < (1u << hw); ++a) {
-            off2[((size_t)mcls << hw) + a] = (uint16_t)run;
-            run += (uint32_t)binom_h(bl.w, mcls - __builtin_popcount(a));
-        }
-    }
-    std::vector<uint8_t> rank8(1u << bl.w);
+    // cross bonds grouped by prefix site: csite = (prefix bit, first, end)
+    std::vector<int32_t> csite;
     {
-        std::vector<int> cnt(bl.w + 1, 0);
-        for (uint32_t v = 0; v < (1u << bl.w); ++v) rank8[v] = (uint8_t)cnt[__builtin_popcount(v)]++;
+        const int nc = (int)cross.size() / 4;
+        std::vector<int> idx(nc);
+        for (int q = 0; q < nc; ++q) idx[q] = q;
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return cross[4 * a] < cross[4 * c]; });
+        std::vector<int32_t> sorted;
+        for (int q : idx) sorted.insert(sorted.end(), cross.begin() + 4 * q, cross.begin() + 4 * q + 4);
+        cross.swap(sorted);
+        for (int q = 0; q < nc; ++q)
+            if (q == 0 || cross[4 * q] != cross[4 * (q - 1)]) csite.insert(csite.end(), {cross[4 * q], q, q + 1});
+            else csite.back() = q + 1;
     }
-    // non-empty prefix blocks, largest first
+    bl.ncsite = (int)csite.size() / 3;
+    bl.npre = (int)pre.size() / 3;
+    bl.ncross = (int)cross.size() / 4;
+    bl.npost = (int)post.size();
+    bl.npost_pad = (bl.npost + 7) / 8 * 8;
+    bl.post.assign(post.begin(), post.end());
+    // target tables indexed by the class-ordered position g of the postfix word;
+    // "no flip" and padding entries point at the kernel's zero slot
+    const uint32_t nlo = 1u << L;
+    const uint16_t noflip = (uint16_t)binom_h(L, L / 2);  // the kernel's zero slot
+    std::vector<uint16_t> ptab((size_t)bl.npost_pad * nlo, noflip), xtab((size_t)slot_site.size() * nlo);
+    for (uint32_t g = 0; g < nlo; ++g) {
+        const uint32_t l = b->h_lo_list[g];
+        for (int q = 0; q < bl.npost; ++q) {
+            int i = b->bonds[post[q]].i, j = b->bonds[post[q]].j;
+            uint16_t v = noflip;
+            if (((l >> i) & 1) != ((l >> j) & 1)) v = (uint16_t)b->h_lo_rank[l ^ (1u << i) ^ (1u << j)];
+            ptab[(size_t)q * nlo + g] = v;
+        }
+        for (size_t q = 0; q < slot_site.size(); ++q)
+            xtab[q * nlo + g] = (uint16_t)b->h_lo_rank[l ^ (1u << slot_site[q])];
+    }
+    // non-empty prefix blocks in ascending order
     std::vector<uint32_t> order;
     for (uint64_t h = 0; h < (1ull << P); ++h) {
         int m = nup - __builtin_popcountll(h);
         if (m >= 0 && m <= L) order.push_back((uint32_t)h);
     }
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t c) {
-        return binom_h(L, nup - __builtin_popcount(a)) > binom_h(L, nup - __builtin_popcount(c));
-    });
     bl.nblk = (int64_t)order.size();
     bl.maxblk = (int)binom_h(L, L / 2);
-    (void)N;
     auto up = [](auto **dst, const auto &v) -> xd_status {
         using E = typename std::remove_reference<decltype(v)>::type::value_type;
         XD_CUDA(cudaMalloc((void **)dst, std::max<size_t>(1, v.size()) * sizeof(E)));
@@ -273,12 +389,12 @@ xd_status block_layout_build(xd_basis_s *b) {
         return XD_OK;
     };
     XD_TRY(up(&bl.d_order, order));
-    XD_TRY(up(&bl.d_csr_off, off));
-    XD_TRY(up(&bl.d_csr, ent));
-    XD_TRY(up(&bl.d_off2, off2));
-    XD_TRY(up(&bl.d_rank8, rank8));
+    XD_TRY(up(&bl.d_ptab, ptab));
+    XD_TRY(up(&bl.d_xtab, xtab));
+    XD_TRY(up(&bl.d_postid, post));
     XD_TRY(up(&bl.d_pre, pre));
     XD_TRY(up(&bl.d_cross, cross));
+    XD_TRY(up(&bl.d_csite, csite));
     bl.ok = true;
     return XD_OK;
 }
@@ -286,34 +402,36 @@ xd_status block_layout_build(xd_basis_s *b) {
 void block_layout_free(xd_basis_s *b) {
     BlockLayoutHost &bl = b->blk;
     cudaFree(bl.d_order);
-    cudaFree(bl.d_csr_off);
-    cudaFree(bl.d_csr);
-    cudaFree(bl.d_off2);
-    cudaFree(bl.d_rank8);
+    cudaFree(bl.d_ptab);
+    cudaFree(bl.d_xtab);
+    cudaFree(bl.d_postid);
     cudaFree(bl.d_pre);
     cudaFree(bl.d_cross);
+    cudaFree(bl.d_csite);
     bl = BlockLayoutHost();
 }
 
-// d_post(l) = sum over postfix bonds of J/4 (+1 equal spins, -1 opposite)
+// d_post[g] = sum over postfix bonds of J/4 (+1 equal spins, -1 opposite)
+// for the postfix word at class-ordered position g.
 xd_status block_ham_tables(xd_ham_s *h) {
     const xd_basis_s *b = h->b;
     const uint32_t nlo = 1u << b->L;
     std::vector<double> dpost(nlo, 0.0);
-    for (uint32_t l = 0; l < nlo; ++l) {
+    for (uint32_t g = 0; g < nlo; ++g) {
+        const uint32_t l = b->h_lo_list[g];
         double d = 0.0;
         for (int k : b->blk.post) {
             int i = b->bonds[k].i, j = b->bonds[k].j;
             d += (((l >> i) & 1) == ((l >> j) & 1) ? 0.25 : -0.25) * h->J[k];
         }
-        dpost[l] = d;
+        dpost[g] = d;
     }
     if (!h->d_dpost) XD_CUDA(cudaMalloc((void **)&h->d_dpost, nlo * sizeof(double)));
     XD_CUDA(cudaMemcpy(h->d_dpost, dpost.data(), nlo * sizeof(double), cudaMemcpyHostToDevice));
     return XD_OK;
 }
 
-template <typename T>
+template <typename T, int L, int NBUF>
 static xd_status launch_block(const xd_ham_s *h, const void *x, void *y, cudaStream_t st) {
     const xd_basis_s *b = h->b;
     const BlockLayoutHost &bl = b->blk;
@@ -321,38 +439,67 @@ static xd_status launch_block(const xd_ham_s *h, const void *x, void *y, cudaStr
     p.u = b->u1view();
     p.order = bl.d_order;
     p.nblk = bl.nblk;
-    p.csr_off = bl.d_csr_off;
-    p.csr = bl.d_csr;
-    p.off2 = bl.d_off2;
-    p.rank8 = bl.d_rank8;
-    p.w = bl.w;
-    p.dpost = h->d_dpost;
+    p.ptab = bl.d_ptab;
+    p.xtab = bl.d_xtab;
+    p.post = bl.d_postid;
+    p.npost = bl.npost;
+    p.npost_pad = bl.npost_pad;
     p.J = h->d_J;
+    p.dpost = h->d_dpost;
+    double q = 0.0;
+    for (int k = 0; k < b->nb; ++k) {
+        int i = std::min(b->bonds[k].i, b->bonds[k].j), j = std::max(b->bonds[k].i, b->bonds[k].j);
+        if (i < b->L && j >= b->L) q += h->J[k];
+    }
+    p.jcross = 0.25 * q;
     p.pre = bl.d_pre;
     p.npre = bl.npre;
     p.cross = bl.d_cross;
     p.ncross = bl.ncross;
+    p.csite = bl.d_csite;
+    p.ncsite = bl.ncsite;
     p.nb = b->nb;
-    p.maxblk = bl.maxblk;
-    const SmemLayout<T> lay(p);
-    auto kern = k_block_apply<T>;
+    p.maxblk = Geo<L>::maxblk;
+    const SmemLayout<T> lay(p, NBUF);
+    auto kern = k_block_apply<T, L, NBUF>;
     XD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total));
     int per_sm = 0;
-    XD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, lay.total));
+    XD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBT, lay.total));
     if (per_sm < 1) {
         set_error("block kernel: %zu bytes of shared memory do not fit", lay.total);
         return XD_ERANGE;
     }
     grid_for(1, 1, 1);
-    const int grid = (int)std::min<int64_t>(bl.nblk, (int64_t)g_num_sms * per_sm);
-    kern<<<grid, 256, lay.total, st>>>(p, (const T *)x, (T *)y);
+    const int grid = (int)std::min<int64_t>(p.nblk, (int64_t)g_num_sms * per_sm);
+    kern<<<grid, kBT, lay.total, st>>>(p, (const T *)x, (T *)y);
     XD_CUDA(cudaGetLastError());
     return XD_OK;
 }
 
+template <typename T, int L>
+static xd_status launch_nb(const xd_ham_s *h, const void *x, void *y, cudaStream_t st) {
+    // two neighbour buffers when two CTAs with three block buffers each fit
+    const size_t blk = (size_t)Geo<L>::maxblk * sizeof(T);
+    if (6 * blk <= 220 * 1024) return launch_block<T, L, 2>(h, x, y, st);
+    return launch_block<T, L, 1>(h, x, y, st);
+}
+
+template <typename T>
+static xd_status launch_L(const xd_ham_s *h, const void *x, void *y, cudaStream_t st) {
+    switch (h->b->L) {
+        case 10: return launch_nb<T, 10>(h, x, y, st);
+        case 11: return launch_nb<T, 11>(h, x, y, st);
+        case 12: return launch_nb<T, 12>(h, x, y, st);
+        case 13: return launch_nb<T, 13>(h, x, y, st);
+        case 14: return launch_nb<T, 14>(h, x, y, st);
+        case 15: return launch_nb<T, 15>(h, x, y, st);
+        default: return launch_nb<T, 16>(h, x, y, st);
+    }
+}
+
 xd_status block_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, cudaStream_t st) {
-    if (dt == XD_F64) return launch_block<double>(h, x, y, st);
-    return launch_block<float>(h, x, y, st);
+    if (dt == XD_F64) return launch_L<double>(h, x, y, st);
+    return launch_L<float>(h, x, y, st);
 }
 
 }  // namespace xd
