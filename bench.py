@@ -31,6 +31,24 @@ LX, LY, J1, J2 = 4, 8, 1.0, 0.5
 N, NUP = LX * LY, LX * LY // 2
 SEED = 2
 METRIC = "Hamiltonian elements applied/s for H.v at N=32 Sz=0 (4x8 J1-J2)"
+FORM_NOTE = {
+    "f32": "FP32 vector storage and FP32 products (Lanczos dots, alpha, beta in FP64-class arithmetic)",
+    "f64": "FP64 vectors, FP64 products (plain form)",
+}
+# dram__bytes_read.sum + dram__bytes_write.sum of one apply launch at this
+# workload (ncu, profiles/apply_4x8_*.md); None until measured for the
+# kernel as it stands
+TRAFFIC = {"f32": 64.23e9, "f64": 146.00e9}
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
 WORKLOAD = "4x8 periodic J1-J2 Heisenberg (J1=1, J2=0.5), N=32, Sz=0, dim 601080390, y = H x"
 
 
@@ -149,7 +167,17 @@ def main():
     ap.add_argument("--form", default="f32", choices=["f64", "f32"])
     ap.add_argument("--lanczos-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only", action="store_true", help="time the headline form only")
+    ap.add_argument("--lattice", default="4x8",
+                    help="LxxLy of the periodic J1-J2 lattice (4x8 is the benchmark; smaller "
+                         "ones serve ncu captures, e.g. 4x7)")
     args = ap.parse_args()
+    global LX, LY, N, NUP, WORKLOAD
+    LX, LY = (int(v) for v in args.lattice.lower().split("x"))
+    N, NUP = LX * LY, LX * LY // 2
+    if args.lattice != "4x8":
+        WORKLOAD = (f"{LX}x{LY} periodic J1-J2 Heisenberg (J1=1, J2=0.5), N={N}, Sz=0, "
+                    f"dim {math.comb(N, NUP)}, y = H x")
     if args.impl == "reference":
         return run_reference(args)
 
@@ -162,6 +190,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    torch.cuda.synchronize()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -171,57 +200,79 @@ def main():
     basis = api.Basis(N, NUP, bonds)
     ham = api.Hamiltonian(basis, J)
     dim = basis.dim
-    dtype = torch.float64 if args.form == "f64" else torch.float32
-    esize = 8 if args.form == "f64" else 4
-    x = api.random_vector(dim, SEED, dtype)
-    y = torch.empty_like(x)
     elements = elements_per_matvec(bonds)
-    compulsory = 2 * esize * dim
     stream = torch.cuda.current_stream()
+    hbm, peak_kind = peaks()
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(max(3, args.warmup)):
-        ham.apply(x, out=y)
-    barrier()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
-    with Clocks(local) as clk:
+    def time_form(form, steps, warmup, clocks=None):
+        """K timed applies on resident inputs; per-launch CUDA events on the
+        launching stream; returns (ms per step over the whole region, mean
+        kernel ms)."""
+        dtype = torch.float64 if form == "f64" else torch.float32
+        x = api.random_vector(dim, SEED, dtype)
+        y = torch.empty_like(x)
+        for _ in range(max(3, warmup)):
+            ham.apply(x, out=y)
         barrier()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        for k in range(args.steps):
-            ev[2 * k].record(stream)
-            ham.apply(x, out=y)
-            ev[2 * k + 1].record(stream)
-        t1.record(stream)
-        barrier()
-    total_ms = t0.elapsed_time(t1)
-    per = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps)]
-    kern_ms = statistics.mean(per)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * elements / (ms_per_step / 1e3)
-    hbm, peak_kind = peaks()
-    achieved = compulsory / (kern_ms / 1e3) / 1e9
+        ctx = clocks if clocks is not None else _Null()
+        with ctx:
+            barrier()
+            t0.record(stream)
+            for k in range(steps):
+                ev[2 * k].record(stream)
+                ham.apply(x, out=y)
+                ev[2 * k + 1].record(stream)
+            t1.record(stream)
+            barrier()
+        total = t0.elapsed_time(t1)
+        if dist is not None:
+            t = torch.tensor([total], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        kern = statistics.mean(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(steps))
+        del x, y
+        torch.cuda.empty_cache()
+        return total / steps, kern
 
-    # Lanczos seconds per iteration (same workload and storage form)
-    lz = ham.lanczos(max_iter=args.lanczos_steps, seed=SEED, storage=dtype)
-    t_l = time.perf_counter()
-    lz = ham.lanczos(max_iter=args.lanczos_steps, seed=SEED, storage=dtype)
-    lz_s = (time.perf_counter() - t_l) / max(1, lz["n_iter"])
+    def lanczos_s_per_iter(form, iters):
+        dtype = torch.float64 if form == "f64" else torch.float32
+        ham.lanczos(max_iter=2, seed=SEED, storage=dtype)
+        t = time.perf_counter()
+        info = ham.lanczos(max_iter=iters, seed=SEED, storage=dtype)
+        return (time.perf_counter() - t) / max(1, info["n_iter"])
 
-    # end to end through the public API with pinned host buffers
-    xh = x.cpu().pin_memory()
+    forms = {}
+    head = args.form
+    clk = Clocks(local)
+    for form in (["f64", "f32"] if head == "f32" else ["f32", "f64"]) if not args.only else [head]:
+        steps = args.steps if form == head else max(3, args.steps // 4)
+        ms_step, kern_ms = time_form(form, steps, args.warmup, clk if form == head else None)
+        esize = 8 if form == "f64" else 4
+        compulsory = 2 * esize * dim
+        achieved = compulsory / (kern_ms / 1e3) / 1e9
+        forms[form] = {
+            "value": world * elements / (ms_step / 1e3), "unit": "elements/s", "ms_per_step": ms_step,
+            "steps": steps, "kernel_ms": kern_ms, "hbm_gbs_compulsory": achieved,
+            "roofline_frac": achieved / hbm,
+            "lanczos_s_per_iter": lanczos_s_per_iter(form, args.lanczos_steps),
+        }
+    fh = forms[head]
+    esize = 8 if head == "f64" else 4
+    # end to end through the public API with pinned host buffers (headline form)
+    dtype = torch.float64 if head == "f64" else torch.float32
+    xh = api.random_vector(dim, SEED, dtype).cpu().pin_memory()
     yh = torch.empty_like(xh).pin_memory()
-    xd = torch.empty_like(x)
-    e2e_steps = max(2, min(args.steps, 5))
+    xd = torch.empty(dim, dtype=dtype, device="cuda")
+    y = torch.empty_like(xd)
+    e2e_steps = max(2, min(args.steps, 4))
     ham.apply(xd.copy_(xh, non_blocking=True), out=y)
     yh.copy_(y, non_blocking=True)
     barrier()
@@ -235,27 +286,28 @@ def main():
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    del xh, yh, xd
+    del xh, yh, xd, y
 
     line = {
-        "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.form == "f64" else "f32",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": args.form, "dim": dim, "bonds": len(bonds),
+        "metric": METRIC, "value": fh["value"], "unit": "elements/s", "n_gpus": world,
+        "steps": fh["steps"], "warmup": args.warmup, "ms_per_step": fh["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": head, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": FORM_NOTE[head], "dim": dim, "bonds": len(bonds),
                    "elements_per_matvec": elements, "seed": SEED,
-                   "l2": "inputs larger than L2 (x, y %.1f GB each)" % (esize * dim / 1e9),
+                   "l2": "inputs larger than L2 (x, y %.1f GB each), no flush" % (esize * dim / 1e9),
                    "parallelism": f"replicas{world}"},
-        "hbm_gbs_compulsory": achieved,
-        "lanczos_s_per_iter": lz_s,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
-                     "note": f"compulsory bytes 2*{esize}*dim per matvec; peak {peak_kind}"},
+        "hbm_gbs_compulsory": fh["hbm_gbs_compulsory"],
+        "lanczos_s_per_iter": fh["lanczos_s_per_iter"],
+        "roofline": {"bound": "hbm", "achieved": fh["hbm_gbs_compulsory"], "peak": hbm, "unit": "GB/s",
+                     "frac": fh["roofline_frac"], "traffic": TRAFFIC.get(head),
+                     "kernel": "k_block_apply", "peak_kind": peak_kind,
+                     "note": f"achieved = compulsory 2*{esize}*dim bytes per H.v / mean launch time"},
+        "forms": forms,
         "clocks": clk.summary(),
         "e2e": {"value": world * elements / (e2e_ms / 1e3), "unit": "elements/s",
                 "h2d_bytes_per_step": esize * dim, "d2h_bytes_per_step": esize * dim},
-        "gpu_launches": args.steps,
+        "gpu_launches": fh["steps"],
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
