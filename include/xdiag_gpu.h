@@ -133,6 +133,26 @@ xd_status xd_apply(xd_ham h, const void *x, void *y, xd_dtype dtype,
 xd_status xd_apply_bilinear(xd_ham h, const void *g, const void *x,
                             xd_dtype dtype, double *dJ, xd_stream stream);
 
+/* Same per-bond bilinear forms as xd_apply_bilinear, for callers that must
+ * not have the library allocate device memory: a process whose allocator
+ * owns all of the GPU's memory (a pool or a fixed budget set at start-up),
+ * or a latency-sensitive loop where cudaMalloc/cudaFree may synchronise the
+ * device.  This call allocates nothing: its partial sums live in one fixed
+ * array of 608 x 256 doubles (1.19 MiB) inside the library, which every GPU
+ * that loads the library keeps until the process exits.  The paper has no
+ * counterpart; it is an interface convenience of this library.
+ * U(1) blocks only; dtype XD_F64 or XD_F32; g, x device [dim] vectors;
+ * dJ device [nb] doubles, caller-owned.  Blocks with more than 256 bonds are
+ * rejected with XD_ERANGE (xd_apply_bilinear has no such limit).
+ * The first call on each device looks up that array's device address (this
+ * may load the library's device code on that device); make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents, so calls that overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller.  Asynchronous
+ * on `stream`. */
+xd_status xd_apply_bilinear_noalloc(xd_ham h, const void *g, const void *x,
+                                    xd_dtype dtype, double *dJ, xd_stream stream);
+
 /* ---------------------------------------------------------------- Lanczos */
 
 /* Lanczos tridiagonalisation from the seeded normal start vector

@@ -9,6 +9,9 @@
 //   a5  gather x_c and accumulate.
 // The diagonal is written as J_sum/4 - sum over flipped bonds of J_b/2.
 
+#include <algorithm>
+#include <mutex>
+
 #include "xd_internal.cuh"
 
 namespace xd {
@@ -241,4 +244,100 @@ xd_status u1_bilinear(const xd_ham_s *h, const void *g, const void *x, xd_dtype 
     return XD_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the per-bond bilinear forms.
+//
+// Some callers cannot let a library call cudaMalloc: a process whose own
+// allocator owns all device memory (a pool sized once at start-up, or a hard
+// memory budget), or a latency-sensitive loop where cudaMalloc/cudaFree may
+// synchronise the device.  xd_apply_bilinear keeps its per-CTA partial sums
+// in a workspace that the handle allocates (and grows) on demand; this
+// variant keeps them in the fixed file-scope array below instead, so the
+// call itself allocates nothing.  Every call, on every stream, shares this
+// one array and leaves the last call's partials in it; nothing in it needs
+// to start at zero (each launch writes every partial it later reads), but
+// two calls that overlap on the GPU race on it and give wrong results.
+
+namespace {
+
+// [kNoAllocCtas][kNoAllocBonds] partial sums: 608 x 256 doubles = 1.19 MiB,
+// held on every GPU that loads the library until the process exits.
+constexpr int kNoAllocCtas = 608;
+constexpr int kNoAllocBonds = 256;
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocCtas * kNoAllocBonds];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the array on the current device.  In host code the name
+// g_noalloc_partials is only a host-side stand-in, so the address comes from
+// cudaGetSymbolAddress, once per device, with that device current.
+xd_status noalloc_scratch(double **out) {
+    int dev = 0;
+    XD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("xd_apply_bilinear_noalloc: device %d beyond the %d supported", dev, kMaxDevices);
+        return XD_ERANGE;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_noalloc_partials)");
+        g_noalloc_ptr[dev] = (double *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return XD_OK;
+}
+
+}  // namespace
+
+}  // namespace xd
+
+extern "C" xd_status xd_apply_bilinear_noalloc(xd_ham h, const void *g, const void *x, xd_dtype dt,
+                                               double *dJ, xd_stream stream) {
+    using namespace xd;
+    if (!h || !g || !x || !dJ) {
+        set_error("xd_apply_bilinear_noalloc: NULL argument");
+        return XD_EINVAL;
+    }
+    const xd_basis_s *b = h->b;
+    if (b->sym) {
+        set_error("xd_apply_bilinear_noalloc: U(1) blocks only (this block is symmetry-adapted)");
+        return XD_EINVAL;
+    }
+    if (dt != XD_F64 && dt != XD_F32) {
+        set_error("xd_apply_bilinear_noalloc: dtype must be XD_F64 or XD_F32");
+        return XD_EINVAL;
+    }
+    const int nb = b->nb;
+    if (nb > kNoAllocBonds) {
+        set_error("xd_apply_bilinear_noalloc: %d bonds exceed the fixed scratch limit of %d bonds "
+                  "(use xd_apply_bilinear)", nb, kNoAllocBonds);
+        return XD_ERANGE;
+    }
+    if (b->dim == 0) return XD_OK;
+    double *part = nullptr;
+    XD_TRY(noalloc_scratch(&part));
+    const U1View u = b->u1view();
+    const int grid = std::min(grid_for(u.dim, kThreads, 4), kNoAllocCtas);
+    const uint64_t *masks = (const uint64_t *)(h->d_bond + nb);
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int b0 = 0; b0 < nb; b0 += kChunk) {
+        if (dt == XD_F64)
+            k_bilinear<double><<<grid, kThreads, 0, st>>>(u, masks, nb, b0, (const double *)g,
+                                                          (const double *)x, part);
+        else
+            k_bilinear<float><<<grid, kThreads, 0, st>>>(u, masks, nb, b0, (const float *)g,
+                                                         (const float *)x, part);
+        XD_CUDA(cudaGetLastError());
+    }
+    k_sum_columns<<<(nb + 127) / 128, 128, 0, st>>>(part, grid, nb, dJ);
+    XD_CUDA(cudaGetLastError());
+    return XD_OK;
+}
+
+namespace xd {
 }  // namespace xd
