@@ -206,6 +206,7 @@ static xd_status check_group(const xd_basis_s *b) {
 
 static void free_basis(xd_basis_s *b) {
     block_layout_free(b);
+    spmm_layout_free(b);
     cudaFree(b->d_hi_off);
     cudaFree(b->d_lo_rank);
     cudaFree(b->d_lo_list);
@@ -317,6 +318,7 @@ xd_status xd_basis_create(int N, int nup, const int32_t *bonds, int nb, const xd
     xd_status s = build_u1(b);
     if (s == XD_OK && b->sym) s = sym_build(b);
     if (s == XD_OK && block_layout_wanted(b)) s = block_layout_build(b);
+    if (s == XD_OK && spmm_layout_wanted(b)) s = spmm_layout_build(b);
     if (s != XD_OK) {
         free_basis(b);
         return s;
@@ -426,6 +428,7 @@ static xd_status set_J(xd_ham_s *h, const double *J) {
     XD_CUDA(cudaMemcpy(h->d_bond, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice));
     if (b->sym && !h->d_symtab) XD_TRY(sym_ham_tables(h));
     if (b->blk.ok) XD_TRY(block_ham_tables(h));
+    if (b->spmm.ok) XD_TRY(spmm_ham_tables(h));
     return XD_OK;
 }
 
@@ -471,6 +474,8 @@ void xd_ham_destroy(xd_ham h) {
     cudaFree(h->d_lzpart);
     cudaFree(h->d_symtab);
     cudaFree(h->d_dpost);
+    cudaFree(h->d_sp_dpost);
+    cudaFree(h->d_sp_jhalf);
     cudaFree(h->d_part);
     cudaFree(h->d_scal);
     delete h;

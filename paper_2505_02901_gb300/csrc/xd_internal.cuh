@@ -85,6 +85,20 @@ struct BlockLayoutHost {
     int ncsite = 0;
 };
 
+// Batched FP32 layout of a large U(1) block (xd_u1_spmm.cu).
+struct SpmmLayoutHost {
+    bool ok = false;
+    int L = 0, P = 0, npost = 0, npost_pad = 0, npre = 0, ncross = 0, ncsite = 0, maxblk = 0, maxpa = 0;
+    int64_t nitems = 0;
+    std::vector<uint32_t> h_lo_off, h_lo_list;
+    std::vector<int> post, cross_ids;
+    int64_t *d_hi_off = nullptr, *d_pcsr_off = nullptr;
+    uint32_t *d_lo_off = nullptr, *d_lo_list = nullptr, *d_items = nullptr;
+    uint16_t *d_ptab = nullptr, *d_xtab = nullptr, *d_postid = nullptr;
+    int32_t *d_pre = nullptr, *d_cross = nullptr, *d_csite = nullptr;
+    uint64_t *d_pcsr = nullptr;
+};
+
 }  // namespace xd
 
 struct xd_basis_s {
@@ -111,6 +125,7 @@ struct xd_basis_s {
     int nchunk = 0;
     double *d_chi = nullptr;  // [G][2]
     xd::BlockLayoutHost blk;
+    xd::SpmmLayoutHost spmm;
 
     xd::U1View u1view() const;
     xd::SymView symview() const;
@@ -128,6 +143,9 @@ struct xd_ham_s {
     int lzpart_n = 0;
     double *d_symtab = nullptr;     // symmetric blocks: sqrt ratios [(G+1)^2] | bond orbit ids
     double *d_dpost = nullptr;      // block layout: postfix diagonal per L-bit word
+    float *d_sp_dpost = nullptr;    // batched layout: postfix diagonal per class position
+    float *d_sp_jhalf = nullptr;    // batched layout: J/2 per bond
+    float sp_jcross = 0.f;          // batched layout: sum over cross bonds of J/4
 };
 
 namespace xd {
@@ -154,6 +172,12 @@ xd_status block_layout_build(xd_basis_s *b);
 void block_layout_free(xd_basis_s *b);
 xd_status block_ham_tables(xd_ham_s *h);
 xd_status block_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, cudaStream_t st);
+// batched FP32 U(1) product (xd_u1_spmm.cu)
+bool spmm_layout_wanted(const xd_basis_s *b);
+xd_status spmm_layout_build(xd_basis_s *b);
+void spmm_layout_free(xd_basis_s *b);
+xd_status spmm_ham_tables(xd_ham_s *h);
+xd_status spmm_apply(const xd_ham_s *h, const void *x, void *y, cudaStream_t st);
 // forget cached batch plans that use this handle (xd_batch.cu)
 void batch_forget(const xd_ham_s *h);
 // workspace helper

@@ -52,7 +52,7 @@ def test_apply_f64_matches_oracle(orc, case):
     assert np.abs(y - yo).max() <= 1e-12 * np.abs(yo).max()
 
 
-@pytest.mark.parametrize("case", [3, 6, 9, 12, 13, 14, 16, 17])
+@pytest.mark.parametrize("case", [3, 6, 9, 12, 13, 14, 16, 17, 18])
 @pytest.mark.parametrize("nvec", [1, 2, 4, 8])
 def test_apply_f32_and_multi_rhs(orc, case, nvec):
     A = api()
@@ -137,21 +137,22 @@ def test_errors_are_statuses(orc):
         A.Hamiltonian(A.Basis(8, 4, W.chain(8)), [1, 2, 3, 4, 5, 6, 7, float("nan")])
 
 
-def test_ladder28_full_size(orc):
-    """C3 workload size: 14x2 ladder, 56 bonds, dim 40,116,600, FP64;
-    sampled rows against the counting-index oracle."""
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 5e-6)])
+def test_ladder28_full_size(orc, dtype, tol):
+    """C3 workload size: 14x2 ladder, 56 bonds (each rung twice), dim
+    40,116,600; sampled rows against the counting-index oracle."""
     A = api()
     bonds = W.ladder(14, 2)
     J = W.uniform_couplings(56, 3)
     ham = A.Hamiltonian(A.Basis(28, 14, bonds), J)
     assert ham.dim == 40116600
     seed = 77
-    x = A.random_vector(ham.dim, seed, torch.float64)
+    x = A.random_vector(ham.dim, seed, dtype)
     y = ham.apply(x)
     rows = np.concatenate([[0, ham.dim - 1], np.random.default_rng(1).integers(0, ham.dim, 3000)])
     yo = orc.apply_rows_rng(28, 14, bonds, J, seed, rows)
-    ys = y[torch.from_numpy(rows).cuda()].cpu().numpy()
-    assert rel_l2(ys, yo) <= 1e-12
+    ys = y[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+    assert rel_l2(ys, yo) <= tol
 
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 5e-6)])
