@@ -213,9 +213,11 @@ static void free_basis(xd_basis_s *b) {
     cudaFree(b->d_lo_off);
     cudaFree(b->d_reps);
     cudaFree(b->d_stab);
-    cudaFree(b->d_bits);
-    cudaFree(b->d_cum);
+    cudaFree(b->d_rs);
     cudaFree(b->d_act);
+    cudaFree(b->d_minrot);
+    cudaFree(b->d_amask);
+    cudaFree(b->d_tg);
     cudaFree(b->d_chi);
     delete b;
 }
@@ -244,11 +246,15 @@ xd::SymView xd_basis_s::symview() const {
     v.dim = dim;
     v.reps = d_reps;
     v.stab = d_stab;
-    v.bits = d_bits;
-    v.cum = d_cum;
+    v.rs = d_rs;
     v.act = d_act;
     v.nchunk = nchunk;
     v.u1 = u1view();
+    v.tx = tx;
+    v.ty = ty;
+    v.minrot = d_minrot;
+    v.amask = d_amask;
+    v.tg = d_tg;
     return v;
 }
 
@@ -374,10 +380,10 @@ xd_status xd_basis_index(xd_basis b, uint64_t s, int64_t *idx) {
         *idx = k;
         return XD_OK;
     }
-    uint64_t w;
-    int64_t c;
-    XD_CUDA(cudaMemcpy(&w, b->d_bits + (k >> 6), sizeof w, cudaMemcpyDeviceToHost));
-    XD_CUDA(cudaMemcpy(&c, b->d_cum + (k >> 6), sizeof c, cudaMemcpyDeviceToHost));
+    ulonglong2 wc;
+    XD_CUDA(cudaMemcpy(&wc, b->d_rs + (k >> 6), sizeof wc, cudaMemcpyDeviceToHost));
+    const uint64_t w = wc.x;
+    const int64_t c = (int64_t)wc.y;
     if (!((w >> (k & 63)) & 1)) {
         *idx = -1;
         return XD_OK;

@@ -59,11 +59,16 @@ struct SymView {
     int64_t dim;
     const uint64_t *reps;   // [dim]
     const uint8_t *stab;    // [dim] |Stab(r)|
-    const uint64_t *bits;   // [ceil(dimU1 / 64)]
-    const int64_t *cum;     // [ceil(dimU1 / 64) + 1]
+    const ulonglong2 *rs;   // [ceil(dimU1 / 64)]: (member bits, members before the word)
     const uint64_t *act;    // [G][nchunk][256] byte tables of the action
     int nchunk;
     U1View u1;
+    // translation group of an Lx x Ly torus (site x + Lx*y), when detected:
+    // tx = Lx (0 otherwise), ty = Ly; minrot/amask: smallest rotation of an
+    // Lx-bit row and the rotations reaching it; tg[a + Lx*b] = group index
+    int tx, ty;
+    const uint8_t *minrot, *amask;
+    const int16_t *tg;
 };
 
 struct Bond {
@@ -119,10 +124,12 @@ struct xd_basis_s {
     int64_t dim = 0;
     uint64_t *d_reps = nullptr;
     uint8_t *d_stab = nullptr;
-    uint64_t *d_bits = nullptr;
-    int64_t *d_cum = nullptr;
+    ulonglong2 *d_rs = nullptr;      // rank/select words: (bits, count before)
     uint64_t *d_act = nullptr;
     int nchunk = 0;
+    int tx = 0, ty = 0;              // detected torus translation group
+    uint8_t *d_minrot = nullptr, *d_amask = nullptr;
+    int16_t *d_tg = nullptr;
     double *d_chi = nullptr;  // [G][2]
     xd::BlockLayoutHost blk;
     xd::SpmmLayoutHost spmm;

@@ -96,11 +96,12 @@ __device__ __forceinline__ void block_store(double v, double *__restrict__ part)
     }
 }
 
-// w = a w + c z (z may be NULL);  part = <w, v> (v may be NULL: no dot)
+// w = a w + c z (z may be NULL); part = <w, v> for mode 1, <w, w> (the new
+// w with itself) for mode 2, no dot for mode 0.  v never aliases w.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_axpby_dot(int64_t n, T *__restrict__ w, T a,
                                                         const T *__restrict__ z, T c,
-                                                        const T *__restrict__ v,
+                                                        const T *__restrict__ v, int mode,
                                                         double *__restrict__ part) {
     typename AccOf<T>::A acc;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -108,9 +109,10 @@ __global__ void __launch_bounds__(kThreads) k_axpby_dot(int64_t n, T *__restrict
         T t = a * w[i];
         if (z) t += c * z[i];
         w[i] = t;
-        if (v) acc.add(t, v[i]);
+        if (mode == 1) acc.add(t, v[i]);
+        else if (mode == 2) acc.add(t, t);
     }
-    if (part) block_store(acc.get(), part);
+    if (mode) block_store(acc.get(), part);
 }
 
 // psi += c u
@@ -269,7 +271,10 @@ struct LzWork {
 template <typename T>
 static xd_status lz_axpby(int64_t n, T *w, double a, const T *z, double c, const T *v,
                           const LzWork &lw, cudaStream_t st, double *dot) {
-    k_axpby_dot<T><<<lw.grid, kThreads, 0, st>>>(n, w, (T)a, z, (T)c, v, v ? lw.part : nullptr);
+    // a dot of w with itself reads the updated w, never through a second pointer
+    const int mode = !v ? 0 : (v == w ? 2 : 1);
+    k_axpby_dot<T><<<lw.grid, kThreads, 0, st>>>(n, w, (T)a, z, (T)c, mode == 1 ? v : nullptr, mode,
+                                                 mode ? lw.part : nullptr);
     XD_CUDA(cudaGetLastError());
     if (dot) {
         k_sum<<<1, 32, 0, st>>>(lw.part, lw.grid, lw.scal);

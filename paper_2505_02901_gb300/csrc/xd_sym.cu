@@ -44,7 +44,7 @@ struct Orbit {
     int cnt;       // number of g reaching it = |Stab(rep)|
 };
 
-__device__ __forceinline__ Orbit orbit_min(const SymView &v, uint64_t s) {
+__device__ __forceinline__ Orbit orbit_min_tables(const SymView &v, uint64_t s) {
     Orbit o{~0ull, 0, 0};
     for (int g = 0; g < v.G; ++g) {
         uint64_t t = act(v.act, v.nchunk, g, s);
@@ -57,6 +57,60 @@ __device__ __forceinline__ Orbit orbit_min(const SymView &v, uint64_t s) {
         }
     }
     return o;
+}
+
+// Torus translations: (T_{a,b} s) puts in row y the row (y + b) mod Ly of s
+// rotated by a (new bit x = old bit (x + a) mod Lx).  The smallest image must
+// have the smallest possible top row, rot_a(row (Ly - 1 + b) mod Ly); only
+// the (a, b) reaching that row are evaluated in full.
+__device__ __forceinline__ uint64_t torus_image(uint64_t s, int a, int b, int Lx, int Ly,
+                                                uint64_t rowmask) {
+    uint64_t w = 0;
+    for (int y = 0; y < Ly; ++y) {
+        int ys = y + b;
+        if (ys >= Ly) ys -= Ly;
+        const uint64_t r = (s >> (Lx * ys)) & rowmask;
+        const uint64_t rr = ((r >> a) | (r << (Lx - a))) & rowmask;
+        w |= rr << (Lx * y);
+    }
+    return w;
+}
+
+__device__ __forceinline__ Orbit orbit_min_torus(const SymView &v, uint64_t s) {
+    const int Lx = v.tx, Ly = v.ty;
+    const uint64_t rowmask = (1ull << Lx) - 1;
+    int best = 1 << Lx;
+    for (int b = 0; b < Ly; ++b) {
+        int yt = Ly - 1 + b;
+        if (yt >= Ly) yt -= Ly;
+        const int m = __ldg(v.minrot + ((s >> (Lx * yt)) & rowmask));
+        best = min(best, m);
+    }
+    Orbit o{~0ull, 0, 0};
+    for (int b = 0; b < Ly; ++b) {
+        int yt = Ly - 1 + b;
+        if (yt >= Ly) yt -= Ly;
+        const uint32_t row = (uint32_t)((s >> (Lx * yt)) & rowmask);
+        if (__ldg(v.minrot + row) != best) continue;
+        uint32_t am = __ldg(v.amask + row);
+        while (am) {
+            const int a = __ffs(am) - 1;
+            am &= am - 1;
+            const uint64_t w = torus_image(s, a, b, Lx, Ly, rowmask);
+            if (w < o.rep) {
+                o.rep = w;
+                o.u = __ldg(v.tg + a + Lx * b);
+                o.cnt = 1;
+            } else if (w == o.rep) {
+                ++o.cnt;
+            }
+        }
+    }
+    return o;
+}
+
+__device__ __forceinline__ Orbit orbit_min(const SymView &v, uint64_t s) {
+    return v.tx ? orbit_min_torus(v, s) : orbit_min_tables(v, s);
 }
 
 __device__ __forceinline__ uint64_t find_block(const int64_t *__restrict__ hi_off, uint64_t lo,
@@ -133,6 +187,14 @@ __global__ void k_compact(SymView v, int64_t nwords, const uint64_t *__restrict_
             ++out;
         }
     }
+}
+
+// rank/select words: member bits and the number of members before the word
+__global__ void k_interleave(int64_t nwords, const uint64_t *__restrict__ bits,
+                             const int64_t *__restrict__ cum, ulonglong2 *__restrict__ rs) {
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords;
+         w += (int64_t)gridDim.x * blockDim.x)
+        rs[w] = make_ulonglong2(bits[w], (unsigned long long)cum[w]);
 }
 
 // ---- exclusive scan of int64 counts (three phases, fixed order)
@@ -232,9 +294,10 @@ __global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, const double 
             const Orbit o = orbit_min(v, s ^ mk);
             const int64_t k = __ldg(v.u1.hi_off + (o.rep >> v.u1.L)) +
                               (int64_t)__ldg(v.u1.lo_rank + (o.rep & v.u1.lomask));
-            const uint64_t word = __ldg(v.bits + (k >> 6));
+            const ulonglong2 wc = __ldg(v.rs + (k >> 6));
+            const uint64_t word = wc.x;
             if (!((word >> (k & 63)) & 1)) continue;
-            const int64_t c = __ldg(v.cum + (k >> 6)) + __popcll(word & ((1ull << (k & 63)) - 1));
+            const int64_t c = (int64_t)wc.y + __popcll(word & ((1ull << (k & 63)) - 1));
             const double a = hb * sm_sq[o.cnt * (v.G + 1) + mr];
             if constexpr (CPLX) {
                 const double2 xc = x[c];
@@ -300,9 +363,10 @@ __global__ void __launch_bounds__(kThreads) k_sym_bilinear(SymView v, const uint
                     const Orbit o = orbit_min(v, s ^ mk);
                     const int64_t k = __ldg(v.u1.hi_off + (o.rep >> v.u1.L)) +
                                       (int64_t)__ldg(v.u1.lo_rank + (o.rep & v.u1.lomask));
-                    const uint64_t word = __ldg(v.bits + (k >> 6));
+                    const ulonglong2 wc = __ldg(v.rs + (k >> 6));
+                    const uint64_t word = wc.x;
                     if ((word >> (k & 63)) & 1) {
-                        const int64_t c = __ldg(v.cum + (k >> 6)) +
+                        const int64_t c = (int64_t)wc.y +
                                           __popcll(word & ((1ull << (k & 63)) - 1));
                         const double a = 0.5 * sq[o.cnt * (v.G + 1) + mr];
                         const double cr = a * chi[2 * o.u], ci = a * chi[2 * o.u + 1];
@@ -366,6 +430,48 @@ static xd_status make_tables(xd_basis_s *b) {
                 tab[((size_t)g * b->nchunk + c) * 256 + val] = r;
             }
     }
+    // translation group of an Lx x Ly torus with rows of at most 8 sites?
+    for (int Lx = 2; Lx <= 8 && !b->tx; ++Lx) {
+        if (N % Lx) continue;
+        const int Ly = N / Lx;
+        if (Lx * Ly != G) continue;
+        std::vector<int16_t> tg(G, -1);
+        bool ok = true;
+        for (int g = 0; g < G && ok; ++g) {
+            const int32_t *p = b->perms.data() + (size_t)g * N;
+            const int a = p[0] % Lx, bb = p[0] / Lx;  // image of site 0 fixes (a, b)
+            for (int i = 0; i < N && ok; ++i) {
+                const int x = i % Lx, y = i / Lx;
+                ok = p[i] == ((x + a) % Lx) + Lx * ((y + bb) % Ly);
+            }
+            if (ok && tg[a + Lx * bb] >= 0) ok = false;
+            if (ok) tg[a + Lx * bb] = (int16_t)g;
+        }
+        if (!ok) continue;
+        std::vector<uint8_t> minrot(1u << Lx), amask(1u << Lx);
+        for (uint32_t r = 0; r < (1u << Lx); ++r) {
+            uint32_t m = r, mask = 0;
+            for (int a = 0; a < Lx; ++a) {
+                const uint32_t rr = ((r >> a) | (r << (Lx - a))) & ((1u << Lx) - 1);
+                if (rr < m) {
+                    m = rr;
+                    mask = 1u << a;
+                } else if (rr == m) {
+                    mask |= 1u << a;
+                }
+            }
+            minrot[r] = (uint8_t)m;
+            amask[r] = (uint8_t)mask;
+        }
+        XD_CUDA(cudaMalloc((void **)&b->d_minrot, minrot.size()));
+        XD_CUDA(cudaMalloc((void **)&b->d_amask, amask.size()));
+        XD_CUDA(cudaMalloc((void **)&b->d_tg, tg.size() * sizeof(int16_t)));
+        XD_CUDA(cudaMemcpy(b->d_minrot, minrot.data(), minrot.size(), cudaMemcpyHostToDevice));
+        XD_CUDA(cudaMemcpy(b->d_amask, amask.data(), amask.size(), cudaMemcpyHostToDevice));
+        XD_CUDA(cudaMemcpy(b->d_tg, tg.data(), tg.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
+        b->tx = Lx;
+        b->ty = Ly;
+    }
     XD_CUDA(cudaMalloc((void **)&b->d_act, tab.size() * sizeof(uint64_t)));
     XD_CUDA(cudaMemcpy(b->d_act, tab.data(), tab.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
     std::vector<double> chi(2 * G);
@@ -381,8 +487,10 @@ static xd_status make_tables(xd_basis_s *b) {
 xd_status sym_build(xd_basis_s *b) {
     XD_TRY(make_tables(b));
     const int64_t nwords = (b->dim_u1 + 63) / 64;
-    XD_CUDA(cudaMalloc((void **)&b->d_bits, std::max<int64_t>(1, nwords) * sizeof(uint64_t)));
-    XD_CUDA(cudaMalloc((void **)&b->d_cum, (nwords + 1) * sizeof(int64_t)));
+    uint64_t *d_bits = nullptr;
+    int64_t *d_cum = nullptr;
+    XD_CUDA(cudaMalloc((void **)&d_bits, std::max<int64_t>(1, nwords) * sizeof(uint64_t)));
+    XD_CUDA(cudaMalloc((void **)&d_cum, (nwords + 1) * sizeof(int64_t)));
     int64_t *cnt = nullptr, *sums = nullptr;
     const int64_t nchunks = (nwords + kScanChunk - 1) / kScanChunk;
     XD_CUDA(cudaMalloc((void **)&cnt, std::max<int64_t>(1, nwords) * sizeof(int64_t)));
@@ -393,14 +501,14 @@ xd_status sym_build(xd_basis_s *b) {
     }
     SymView v = b->symview();
     int grid = grid_for(nwords, kThreads, 16);
-    k_mark<<<grid, kThreads>>>(v, b->d_chi, nwords, b->d_bits, cnt);
+    k_mark<<<grid, kThreads>>>(v, b->d_chi, nwords, d_bits, cnt);
     k_scan_sums<<<(unsigned)std::max<int64_t>(1, nchunks), kThreads>>>(cnt, nwords, sums);
     k_scan_serial<<<1, 1>>>(sums, nchunks);
-    k_scan_apply<<<(unsigned)std::max<int64_t>(1, nchunks), kThreads>>>(cnt, nwords, sums, b->d_cum);
+    k_scan_apply<<<(unsigned)std::max<int64_t>(1, nchunks), kThreads>>>(cnt, nwords, sums, d_cum);
     e = cudaGetLastError();
     int64_t total = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&total, sums + nchunks, sizeof total, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_cum + nwords, &total, sizeof total, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_cum + nwords, &total, sizeof total, cudaMemcpyHostToDevice);
     cudaFree(cnt);
     cudaFree(sums);
     if (e != cudaSuccess) return cuda_status(e, "symmetric basis build");
@@ -408,8 +516,17 @@ xd_status sym_build(xd_basis_s *b) {
     XD_CUDA(cudaMalloc((void **)&b->d_reps, std::max<int64_t>(1, total) * sizeof(uint64_t)));
     XD_CUDA(cudaMalloc((void **)&b->d_stab, std::max<int64_t>(1, total)));
     v = b->symview();
-    k_compact<<<grid, kThreads>>>(v, nwords, b->d_bits, b->d_cum, b->d_reps, b->d_stab);
-    XD_CUDA(cudaGetLastError());
+    k_compact<<<grid, kThreads>>>(v, nwords, d_bits, d_cum, b->d_reps, b->d_stab);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_rs, std::max<int64_t>(1, nwords) * sizeof(ulonglong2));
+    if (e == cudaSuccess) {
+        k_interleave<<<grid, kThreads>>>(nwords, d_bits, d_cum, b->d_rs);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d_bits);
+    cudaFree(d_cum);
+    if (e != cudaSuccess) return cuda_status(e, "symmetric basis compaction");
     XD_CUDA(cudaDeviceSynchronize());
     return XD_OK;
 }

@@ -1,0 +1,106 @@
+"""Full-size checks of the benchmark workloads on the GPU.
+
+Where the oracle cannot run the whole product, parity is checked on sampled
+rows (counting index, seeded vector regenerated on the CPU) and through
+properties that hold at any size: Burnside dimensions, valid ascending
+representatives, Hermiticity, agreement of energies between independent
+forms of the product, Euler's identity and finite differences."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2505_02901_gb300 import workloads as W
+from tests.gpu_common import api, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def test_c5b_square6x6_u1_sampled_rows(orc):
+    """6x6 J1-J2, Sz=0 without symmetry: dim 9,075,135,300 (int64 rows), FP32."""
+    A = api()
+    bonds, J = W.square_j1j2(6, 6)
+    ham = A.Hamiltonian(A.Basis(36, 18, bonds), J)
+    assert ham.dim == math.comb(36, 18) == 9075135300
+    seed = 6
+    x = A.random_vector(ham.dim, seed, torch.float32)
+    y = ham.apply(x)
+    del x
+    rows = np.concatenate([[0, ham.dim - 1, 2**32 + 5], np.random.default_rng(6).integers(0, ham.dim, 300)])
+    yo = orc.apply_rows_rng(36, 18, bonds, J, seed, rows)
+    ys = y[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+    assert rel_l2(ys, yo) <= 5e-6
+    del y
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("mx", [0, 1])
+def test_c5a_square6x6_momentum_blocks(orc, mx):
+    """6x6 J1-J2 with its 36 translations at k=(0,0) (real) and k=(pi/3,0)
+    (complex): Burnside dimension, sampled representatives valid and
+    ascending, and <u, H v> = conj <v, H u> at full size."""
+    A = api()
+    bonds, J = W.square_j1j2(6, 6)
+    perms, chi = W.torus_translations(6, 6), W.torus_characters(6, 6, mx, 0)
+    basis = A.Basis(36, 18, bonds, symmetry=(perms, chi))
+    assert basis.dim == orc.burnside_dim(36, 18, perms, chi)
+    assert basis.dim == (252091362 if mx == 0 else 252085716)
+    rng = np.random.default_rng(mx)
+    for k in np.concatenate([[0, basis.dim - 2], rng.integers(0, basis.dim - 1, 40)]):
+        s, s2 = basis.state(int(k)), basis.state(int(k) + 1)
+        assert s < s2
+        r, u, cnt = orc.rep(36, perms, s)
+        assert r == s
+        stab = [g for g in range(36) if orc.act(36, perms[g], s) == s]
+        assert abs(sum(chi[g] for g in stab)) > 0.5 and len(stab) == cnt
+        assert basis.index(s) == k
+    ham = A.Hamiltonian(basis, J)
+    dt = torch.complex128 if basis.is_complex else torch.float64
+    g = torch.Generator(device="cuda").manual_seed(7)
+    u = torch.randn(basis.dim, dtype=dt, device="cuda", generator=g)
+    v = torch.randn(basis.dim, dtype=dt, device="cuda", generator=g)
+    uhv = torch.vdot(u, ham.apply(v)).item()
+    vhu = torch.vdot(v, ham.apply(u)).item()
+    assert abs(uhv - np.conj(vhu)) <= 1e-10 * abs(uhv)
+
+
+def test_c2_square4x8_lanczos_forms_agree(orc):
+    """4x8 J1-J2, 200 Lanczos steps: FP32 vector storage (FP64-class dots)
+    against the FP64 form; the ground energies agree to 1e-6 relative."""
+    A = api()
+    bonds, J = W.square_j1j2(4, 8)
+    ham = A.Hamiltonian(A.Basis(32, 16, bonds), J)
+    e64 = ham.lanczos(max_iter=200, seed=2, storage=torch.float64, nev=2)
+    e32 = ham.lanczos(max_iter=200, seed=2, storage=torch.float32, nev=2)
+    E64, E32 = e64["evals"][0], e32["evals"][0]
+    assert -0.55 * 32 < E64 < -0.45 * 32
+    assert abs(E32 - E64) <= 1e-6 * abs(E64)
+    # converged energy; the residual estimate of the lowest Ritz pair is
+    # blurred by its ghost copy (no reorthogonalisation), so it is looser
+    assert e64["resid"][0] < 1e-5
+
+
+def test_c3_ladder28_gradient(orc):
+    """14-rung ladder, 56 bonds, J ~ U[0.5, 1.5): dE0/dJ by the backward
+    kernel against central differences (h = 1e-5) on two bonds, Euler's
+    identity, and equal derivatives of the two copies of every rung."""
+    A = api()
+    bonds = W.ladder(14, 2)
+    J = W.uniform_couplings(56, 3)
+    ham = A.Hamiltonian(A.Basis(28, 14, bonds), J)
+    e0, psi, info = ham.ground_state(max_iter=200, seed=3)
+    g = ham.energy_grad(psi)
+    assert abs(J @ g - e0) <= 1e-8 * abs(e0)
+    assert np.abs(g[28:42] - g[42:56]).max() < 1e-7
+    h = 1e-5
+    for b in (0, 30):
+        Jp, Jm = J.copy(), J.copy()
+        Jp[b] += h
+        Jm[b] -= h
+        ham.set_couplings(Jp)
+        ep = ham.lanczos(max_iter=200, seed=3)["evals"][0]
+        ham.set_couplings(Jm)
+        em = ham.lanczos(max_iter=200, seed=3)["evals"][0]
+        assert abs((ep - em) / (2 * h) - g[b]) < 1e-5
+    ham.set_couplings(J)

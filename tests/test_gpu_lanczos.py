@@ -28,6 +28,19 @@ def test_chain16_lanczos_f64_and_f32(orc):
     assert abs(info32["evals"][0] - e_ref) <= 1e-6 * abs(e_ref)
 
 
+def test_f32_storage_matches_f64_mid_size(orc):
+    """4x6 J1-J2 (N=24, dim 2,704,156): FP32 vector storage with FP64-class
+    dots against the FP64 form, and the first recurrence coefficients."""
+    A = api()
+    bonds, J = W.square_j1j2(4, 6)
+    ham = A.Hamiltonian(A.Basis(24, 12, bonds), J)
+    r64 = ham.lanczos(max_iter=200, seed=2, storage=torch.float64)
+    r32 = ham.lanczos(max_iter=200, seed=2, storage=torch.float32)
+    assert np.abs(r32["alpha"][:5] - r64["alpha"][:5]).max() < 1e-5
+    assert np.abs(r32["beta"][:5] - r64["beta"][:5]).max() < 1e-5
+    assert abs(r32["evals"][0] - r64["evals"][0]) <= 1e-6 * abs(r64["evals"][0])
+
+
 def test_ground_state_vector_and_residual(orc):
     A = api()
     N = 14
