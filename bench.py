@@ -142,6 +142,104 @@ def cpu_baseline(seconds: float = 12.0):
                       f"{t_used:.1f} s (OpenMP over rows)"}
 
 
+def _event_time(fn, reps=3):
+    """Mean CUDA-event time (ms) of fn() on the current stream after one warm-up."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extra_rows(hbm):
+    """One measurement per remaining hot-path row, each on its own workload:
+    batched product (64 uneven instances, 8 FP32 right-hand sides), per-bond
+    bilinear forms (14-rung ladder, FP64), symmetric products (6x6 J1-J2,
+    k=(0,0) FP64 and k=(pi/3,0) complex128), the 6x6 U(1) product in FP32
+    (dim 9,075,135,300) and the N=16 chain Lanczos.  Fractions are
+    compulsory bytes (vectors read and written once) over time, of the
+    measured HBM bandwidth."""
+    import torch
+
+    from paper_2505_02901_gb300 import api, workloads as W
+    out = {}
+
+    def row(name, ms, bytes_, elements=None, **kw):
+        d = {"ms": ms, "compulsory_gb": bytes_ / 1e9, "hbm_gbs_compulsory": bytes_ / (ms / 1e3) / 1e9,
+             "roofline_frac": bytes_ / (ms / 1e3) / 1e9 / hbm}
+        if elements:
+            d["elements_per_s"] = elements / (ms / 1e3)
+        d.update(kw)
+        out[name] = d
+
+    def elems(N, nup, nb):
+        return math.comb(N, nup) + nb * 2 * math.comb(N - 2, nup - 1)
+
+    # a9: batched persistent form
+    insts = W.batched_instances(64, seed=4)
+    hams, xs, ys, el = [], [], [], 0
+    for k, d in enumerate(insts):
+        h = api.Hamiltonian(api.Basis(d["N"], d["nup"], d["bonds"]), d["J"])
+        hams.append(h)
+        xs.append(torch.randn(h.dim, 8, dtype=torch.float32, device="cuda"))
+        ys.append(torch.empty_like(xs[-1]))
+        el += 8 * elems(d["N"], d["nup"], len(d["bonds"]))
+    rows_total = sum(h.dim for h in hams)
+    ms = _event_time(lambda: api.batch_apply(hams, xs, ys))
+    row("a9_batched_64x8_f32", ms, 2 * 4 * 8 * rows_total, el, rows=rows_total, instances=64, nvec=8)
+    del hams, xs, ys
+    torch.cuda.empty_cache()
+    # a8: bilinear forms on the 56-bond ladder
+    bl = W.ladder(14, 2)
+    h = api.Hamiltonian(api.Basis(28, 14, bl), W.uniform_couplings(56, 3))
+    g = api.random_vector(h.dim, 1, torch.float64)
+    x = api.random_vector(h.dim, 2, torch.float64)
+    ms = _event_time(lambda: h.bilinear(g, x))
+    row("a8_bilinear_ladder28_f64", ms, 2 * 8 * h.dim, h.dim * 56, bonds=56)
+    ms = _event_time(lambda: h.apply(x))
+    row("a5_apply_ladder28_f64", ms, 2 * 8 * h.dim, elems(28, 14, 56))
+    del h, g, x
+    torch.cuda.empty_cache()
+    # a4': symmetric 6x6 blocks
+    b6, J6 = W.square_j1j2(6, 6)
+    for mx in (0, 1):
+        t0 = time.perf_counter()
+        basis = api.Basis(36, 18, b6, symmetry=(W.torus_translations(6, 6), W.torus_characters(6, 6, mx, 0)))
+        build_s = time.perf_counter() - t0
+        h = api.Hamiltonian(basis, J6)
+        dt = torch.complex128 if basis.is_complex else torch.float64
+        es = 16 if basis.is_complex else 8
+        x = torch.randn(basis.dim, dtype=dt, device="cuda")
+        y = torch.empty_like(x)
+        ms = _event_time(lambda: h.apply(x, out=y), reps=2)
+        row(f"a4p_sym6x6_k{mx}0_{'c128' if basis.is_complex else 'f64'}", ms, (2 * es + 9) * basis.dim,
+            dim=basis.dim, basis_build_s=build_s)
+        del basis, h, x, y
+        torch.cuda.empty_cache()
+    # 6x6 U(1) product, FP32 storage
+    h = api.Hamiltonian(api.Basis(36, 18, b6), J6)
+    x = api.random_vector(h.dim, 5, torch.float32)
+    y = torch.empty_like(x)
+    ms = _event_time(lambda: h.apply(x, out=y), reps=2)
+    row("a5_apply_6x6_u1_f32", ms, 2 * 4 * h.dim, elems(36, 18, 144), dim=h.dim)
+    del h, x, y
+    torch.cuda.empty_cache()
+    # a6/a7: chain N=16 Lanczos, 100 steps
+    h = api.Hamiltonian(api.Basis(16, 8, W.chain(16)), [1.0] * 16)
+    h.lanczos(max_iter=100, seed=1)
+    t0 = time.perf_counter()
+    info = h.lanczos(max_iter=100, seed=1)
+    out["a6_a7_lanczos_chain16_f64"] = {"s_per_iter": (time.perf_counter() - t0) / info["n_iter"],
+                                        "n_iter": info["n_iter"], "e0": float(info["evals"][0])}
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -168,6 +266,7 @@ def main():
     ap.add_argument("--lanczos-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only", action="store_true", help="time the headline form only")
+    ap.add_argument("--no-extras", action="store_true", help="skip the per-row measurements")
     ap.add_argument("--lattice", default="4x8",
                     help="LxxLy of the periodic J1-J2 lattice (4x8 is the benchmark; smaller "
                          "ones serve ncu captures, e.g. 4x7)")
@@ -309,6 +408,8 @@ def main():
                 "h2d_bytes_per_step": esize * dim, "d2h_bytes_per_step": esize * dim},
         "gpu_launches": fh["steps"],
     }
+    if rank == 0 and world == 1 and not args.no_extras and args.lattice == "4x8":
+        line["rows"] = extra_rows(hbm)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
