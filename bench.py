@@ -38,7 +38,9 @@ FORM_NOTE = {
 # dram__bytes_read.sum + dram__bytes_write.sum of one apply launch at this
 # workload (ncu, profiles/apply_4x8_*.md); None until measured for the
 # kernel as it stands
-TRAFFIC = {"f32": 64.23e9, "f64": 146.00e9}
+TRAFFIC = {"f32": 75.33e9, "f64": 146.00e9}
+# the kernel each form's product runs at this workload
+KERNEL = {"f32": "k_spmm<12>", "f64": "k_block_apply<double, 16, 1>"}
 
 
 class _Null:
@@ -400,7 +402,7 @@ def main():
         "lanczos_s_per_iter": fh["lanczos_s_per_iter"],
         "roofline": {"bound": "hbm", "achieved": fh["hbm_gbs_compulsory"], "peak": hbm, "unit": "GB/s",
                      "frac": fh["roofline_frac"], "traffic": TRAFFIC.get(head),
-                     "kernel": "k_block_apply", "peak_kind": peak_kind,
+                     "kernel": KERNEL[head], "peak_kind": peak_kind,
                      "note": f"achieved = compulsory 2*{esize}*dim bytes per H.v / mean launch time"},
         "forms": forms,
         "clocks": clk.summary(),
