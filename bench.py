@@ -159,12 +159,29 @@ def _event_time(fn, reps=3):
     return e0.elapsed_time(e1) / reps
 
 
+def _lanczos_steady(ham, dtype, iters, short=2):
+    """Seconds per Lanczos iteration in steady state: the wall time of a run
+    of short + iters steps minus that of a run of `short` steps (both pay the
+    same vector allocation, seeded start vector and normalisation)."""
+    import torch
+    ham.lanczos(max_iter=short, seed=SEED, storage=dtype)
+    ts = []
+    for n in (short, short + iters):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        info = ham.lanczos(max_iter=n, seed=SEED, storage=dtype)
+        ts.append((time.perf_counter() - t, info["n_iter"]))
+    return (ts[1][0] - ts[0][0]) / max(1, ts[1][1] - ts[0][1])
+
+
 def extra_rows(hbm):
     """One measurement per remaining hot-path row, each on its own workload:
     batched product (64 uneven instances, 8 FP32 right-hand sides), per-bond
     bilinear forms (14-rung ladder, FP64), symmetric products (6x6 J1-J2,
     k=(0,0) FP64 and k=(pi/3,0) complex128), the 6x6 U(1) product in FP32
-    (dim 9,075,135,300) and the N=16 chain Lanczos.  Fractions are
+    (dim 9,075,135,300), the paper's N=36 chain U(1) benchmark (product and
+    steady-state Lanczos iteration, FP64 and FP32 storage) and the N=16
+    chain Lanczos.  Fractions are
     compulsory bytes (vectors read and written once) over time, of the
     measured HBM bandwidth."""
     import torch
@@ -231,6 +248,23 @@ def extra_rows(hbm):
     ms = _event_time(lambda: h.apply(x, out=y), reps=2)
     row("a5_apply_6x6_u1_f32", ms, 2 * 4 * h.dim, elems(36, 18, 144), dim=h.dim)
     del h, x, y
+    torch.cuda.empty_cache()
+    # The paper's largest U(1) Lanczos benchmark: the N=36 Heisenberg chain,
+    # Sz=0 (dim 9,075,135,300), one iteration 3.1 s in FP64 on 2304 cores.
+    # FP64 Lanczos keeps three 72.6 GB vectors resident.
+    h = api.Hamiltonian(api.Basis(36, 18, W.chain(36)), [1.0] * 36)
+    for dt, es, tag in ((torch.float64, 8, "f64"), (torch.float32, 4, "f32")):
+        x = api.random_vector(h.dim, 5, dt)
+        y = torch.empty_like(x)
+        ms = _event_time(lambda: h.apply(x, out=y), reps=2)
+        del x, y
+        torch.cuda.empty_cache()
+        s_it = _lanczos_steady(h, dt, 4)
+        torch.cuda.empty_cache()
+        row(f"paper_chain36_u1_{tag}", ms, 2 * es * h.dim, elems(36, 18, 36), dim=h.dim,
+            lanczos_s_per_iter=s_it, paper_fp64_s_per_iter=3.1,
+            paper_hardware="2304 MPI processes (32 x 72-core Xeon Platinum 8360Y)")
+    del h
     torch.cuda.empty_cache()
     # a6/a7: chain N=16 Lanczos, 100 steps
     h = api.Hamiltonian(api.Basis(16, 8, W.chain(16)), [1.0] * 16)
@@ -345,10 +379,7 @@ def main():
 
     def lanczos_s_per_iter(form, iters):
         dtype = torch.float64 if form == "f64" else torch.float32
-        ham.lanczos(max_iter=2, seed=SEED, storage=dtype)
-        t = time.perf_counter()
-        info = ham.lanczos(max_iter=iters, seed=SEED, storage=dtype)
-        return (time.perf_counter() - t) / max(1, info["n_iter"])
+        return _lanczos_steady(ham, dtype, iters)
 
     forms = {}
     head = args.form
