@@ -72,8 +72,8 @@ struct SpSmem {
         xs = o;
         o += (size_t)(maxblk + 1) * kB * sizeof(float);
         al(16);
-        nb = o;
-        o += (size_t)(maxblk + 1) * kB * sizeof(float);
+        nb = o;  // two staging buffers for cross sites
+        o += 2 * (size_t)(maxblk + 1) * kB * sizeof(float);
         al(16);
         jh = o;
         o += (size_t)p.nb * sizeof(float);
@@ -108,7 +108,8 @@ __device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc));
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // Transposed rows are 32 bytes; the halves of rows with bit 2 set are
 // swapped so that 16-byte loads of eight consecutive rows hit distinct banks.
@@ -139,7 +140,8 @@ __global__ void __launch_bounds__(kT, 2) k_spmm(SpParams p, const float *__restr
     extern __shared__ __align__(16) unsigned char smem[];
     const SpSmem lay(p, MB);
     float *xs = (float *)(smem + lay.xs);
-    float *nb = (float *)(smem + lay.nb);
+    float *nbuf = (float *)(smem + lay.nb);
+    constexpr int NBS = (MB + 1) * kB;  // floats per staging buffer
     float *jh = (float *)(smem + lay.jh);
     float *pc = (float *)(smem + lay.pc);
     uint64_t *pl = (uint64_t *)(smem + lay.pl);
@@ -260,53 +262,66 @@ __global__ void __launch_bounds__(kT, 2) k_spmm(SpParams p, const float *__restr
                 }
             }
         }
-        // prefix bonds: per block, coalesced streams from its neighbour blocks.
-        // Eight independent loads are in flight per thread before their uses:
-        // far neighbour blocks come from DRAM and only memory-level
-        // parallelism hides that latency.
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-            const int i = tid + r * kT;
-            if (i < n) {
-#pragma unroll
-                for (int k = 0; k < kB; ++k) {
-                    const int npa = sh_npa[k];
-                    const uint64_t *e = pl + k * p.maxpa;
-                    float a = 0.f;
-#pragma unroll 1
-                    for (int q0 = 0; q0 < npa; q0 += 8) {
-                        float v[8];
-                        float c[8];
-#pragma unroll
-                        for (int w = 0; w < 8; ++w) {
-                            const bool ok = q0 + w < npa;
-                            const uint64_t ev = ok ? e[q0 + w] : 0ull;
-                            c[w] = ok ? jh[(uint32_t)(ev & 4095u)] : 0.f;
-                            v[w] = ok ? __ldg(x + (int64_t)(ev >> 12) + i) : 0.f;
-                        }
-#pragma unroll
-                        for (int w = 0; w < 8; ++w) a = fmaf(c[w], v[w], a);
-                    }
-                    acc[r][k] += a;
-                }
+        // Cross site 0 is staged now, behind the prefix streams.
+        auto stage_site = [&](int c, float *dst) {
+            const int64_t so = noff[c * kB + col];
+            const int sn = nn[c * kB + col];
+            for (int e = tid; e < nmax * kB; e += kT) {
+                const int rr = e >> 3;
+                if (rr < sn) cp_async4(dst + swz(rr, col), x + so + rr);
+                else dst[swz(rr, col)] = 0.f;
             }
+            cp_commit();
+        };
+        if (p.ncsite > 0) stage_site(0, nbuf);
+        // prefix bonds: per block, coalesced streams from its neighbour blocks.
+        // Both rows of a thread load each neighbour, so that sixteen loads
+        // are in flight per thread before their uses: far neighbour blocks
+        // come from DRAM and only memory-level parallelism hides that latency.
+#pragma unroll
+        for (int k = 0; k < kB; ++k) {
+            const int npa = sh_npa[k];
+            const uint64_t *e = pl + k * p.maxpa;
+            float a[K];
+#pragma unroll
+            for (int r = 0; r < K; ++r) a[r] = 0.f;
+#pragma unroll 1
+            for (int q0 = 0; q0 < npa; q0 += 8) {
+                float v[K][8];
+                float c[8];
+#pragma unroll
+                for (int w = 0; w < 8; ++w) {
+                    const bool ok = q0 + w < npa;
+                    const uint64_t ev = ok ? e[q0 + w] : 0ull;
+                    c[w] = ok ? jh[(uint32_t)(ev & 4095u)] : 0.f;
+                    const float *src = x + (int64_t)(ev >> 12);
+#pragma unroll
+                    for (int r = 0; r < K; ++r) {
+                        const int i = tid + r * kT;
+                        v[r][w] = (ok && i < n) ? __ldg(src + i) : 0.f;
+                    }
+                }
+#pragma unroll
+                for (int w = 0; w < 8; ++w)
+#pragma unroll
+                    for (int r = 0; r < K; ++r) a[r] = fmaf(c[w], v[r][w], a[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < K; ++r) acc[r][k] += a[r];
         }
-        // cross bonds: one prefix site at a time, its kB neighbour blocks staged
+        // cross bonds: one prefix site at a time, its kB neighbour blocks
+        // staged; site c + 1 is copied while site c is used
 #pragma unroll 1
         for (int c = 0; c < p.ncsite; ++c) {
-            __syncthreads();  // previous site done with nb
-            {
-                const int64_t so = noff[c * kB + col];
-                const int sn = nn[c * kB + col];
-                for (int e = tid; e < nmax * kB; e += kT) {
-                    const int rr = e >> 3;
-                    if (rr < sn) cp_async4(nb + swz(rr, col), x + so + rr);
-                    else nb[swz(rr, col)] = 0.f;
-                }
-                cp_commit();
+            float *nb = nbuf + (c & 1) * NBS;
+            __syncthreads();  // site c - 1 done with the other buffer
+            if (c + 1 < p.ncsite) {
+                stage_site(c + 1, nbuf + ((c + 1) & 1) * NBS);
+                cp_wait_1();
+            } else {
                 cp_wait_all();
             }
-            __syncthreads();
+            __syncthreads();  // site c staged
             const int q0 = p.csite[3 * c + 1], q1 = p.csite[3 * c + 2];
             const uint32_t m1 = rqm[c], m0 = valid & ~m1;
 #pragma unroll
