@@ -173,7 +173,6 @@ __global__ void __launch_bounds__(kT, 2) k_spmm(SpParams p, const float *__restr
         const int n = (int)(__ldg(p.lo_off + m + 1) - l0);
         const int nm = m > 0 ? (int)(l0 - __ldg(p.lo_off + m - 1)) : 0;
         const int np = m < L ? (int)(__ldg(p.lo_off + m + 2) - __ldg(p.lo_off + m + 1)) : 0;
-        const int nmax = max(nm, np);
         __syncthreads();  // previous item done with shared memory
         {
             // x of the kB blocks, transposed: row r, block k at swz(r, k)
@@ -266,11 +265,7 @@ __global__ void __launch_bounds__(kT, 2) k_spmm(SpParams p, const float *__restr
         auto stage_site = [&](int c, float *dst) {
             const int64_t so = noff[c * kB + col];
             const int sn = nn[c * kB + col];
-            for (int e = tid; e < nmax * kB; e += kT) {
-                const int rr = e >> 3;
-                if (rr < sn) cp_async4(dst + swz(rr, col), x + so + rr);
-                else dst[swz(rr, col)] = 0.f;
-            }
+            for (int e = tid; e < sn * kB; e += kT) cp_async4(dst + swz(e >> 3, col), x + so + (e >> 3));
             cp_commit();
         };
         if (p.ncsite > 0) stage_site(0, nbuf);
@@ -311,6 +306,9 @@ __global__ void __launch_bounds__(kT, 2) k_spmm(SpParams p, const float *__restr
         }
         // cross bonds: one prefix site at a time, its kB neighbour blocks
         // staged; site c + 1 is copied while site c is used
+        uint32_t lw[K];
+#pragma unroll
+        for (int r = 0; r < K; ++r) lw[r] = __ldg(p.lo_list + l0 + min(tid + r * kT, n - 1));
 #pragma unroll 1
         for (int c = 0; c < p.ncsite; ++c) {
             float *nb = nbuf + (c & 1) * NBS;
@@ -328,7 +326,7 @@ __global__ void __launch_bounds__(kT, 2) k_spmm(SpParams p, const float *__restr
             for (int r = 0; r < K; ++r) {
                 const int i = tid + r * kT;
                 if (i < n) {
-                    const uint32_t l = __ldg(p.lo_list + l0 + i);
+                    const uint32_t l = lw[r];
                     float4 xlo, xhi;
                     row8(xs, i, xlo, xhi);
                     const float xv[kB] = {xlo.x, xlo.y, xlo.z, xlo.w, xhi.x, xhi.y, xhi.z, xhi.w};
