@@ -126,53 +126,89 @@ __global__ void __launch_bounds__(kThreads) k_apply(U1View u, const double *__re
     }
 }
 
-// Per-bond bilinear forms: part[cta][b] = sum over the CTA's rows of
-// g_r (S_i.S_j x)_r; each warp reduces its lanes with shuffles into its own
-// shared row, the CTA sums its warps in order.  Bonds in chunks of kChunk.
+// Bonds per launch of the bilinear kernel.
 constexpr int kChunk = 256;
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_bilinear(U1View u, const uint64_t *__restrict__ masks,
-                                                       int nb, int b0, const T *__restrict__ g,
-                                                       const T *__restrict__ x,
-                                                       double *__restrict__ part) {
-    __shared__ double acc[kThreads / 32][kChunk];
+// Per-bond bilinear forms: part[cta][b] = sum over the CTA's rows of
+// g_r (S_i.S_j x)_r (Sec. 3.7 inner, per bond).  With p_r = g_r x_r and
+// P = sum_r p_r,
+//   <g|S_i.S_j|x> = 1/4 sum_r eps_b(s_r) p_r + 1/2 sum_{r: b flips} g_r x_c
+//                 = 1/4 (P - 2 F'_b) + 1/2 F_b,
+// F'_b = sum over flipping rows of p_r and F_b = sum over them of g_r x_c
+// (eps = +1 for parallel, -1 for antiparallel spins): only the flipping
+// bonds of a row cost arithmetic.  A CTA stages the states, g and p of a
+// tile of kBT rows in shared memory; warp w owns bonds w, w + 32, ... of the
+// chunk and every lane walks a fixed set of the tile's rows, so all sums run
+// in a fixed order (lane partials, a fixed shuffle tree, then the CTA
+// partial of each bond).  MBW = most bonds per warp.
+constexpr int kBT = 1024;
+template <typename T, int MBW>
+__global__ void __launch_bounds__(kBT) k_bilinear_bp(U1View u, const uint64_t *__restrict__ masks,
+                                                     int nb, int b0, const T *__restrict__ g,
+                                                     const T *__restrict__ x,
+                                                     double *__restrict__ part) {
+    __shared__ uint64_t sh_s[kBT];
+    __shared__ double sh_g[kBT], sh_p[kBT];
+    __shared__ double sh_red[kBT / 32];
     __shared__ uint64_t sh_range[2];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nbc = min(kChunk, nb - b0);
-    for (int b = lane; b < nbc; b += 32) acc[warp][b] = 0.0;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < u.dim;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = base + threadIdx.x;
-        RowState rs = unrank_tile(u, base, r, sh_range);
-        double gr = 0.0, xr = 0.0;
-        if (rs.valid) {
-            gr = (double)g[r];
-            xr = (double)x[r];
-        }
-        for (int b = 0; b < nbc; ++b) {
-            double v = 0.0;
-            if (rs.valid) {
-                const uint64_t mk = masks[b0 + b];
-                const uint64_t t = rs.s & mk;
-                if (t != 0 && t != mk) {
-                    const int64_t c = rank_of(u, rs.s ^ mk);
-                    v = gr * (0.5 * (double)x[c] - 0.25 * xr);
-                } else {
-                    v = 0.25 * gr * xr;
+    uint64_t mk[MBW];
+    double F[MBW], Fd[MBW];
+#pragma unroll
+    for (int j = 0; j < MBW; ++j) {
+        const int b = warp + 32 * j;
+        mk[j] = b < nbc ? __ldg(masks + b0 + b) : 0ull;
+        F[j] = 0.0;
+        Fd[j] = 0.0;
+    }
+    double P = 0.0;
+    for (int64_t base = (int64_t)blockIdx.x * kBT; base < u.dim; base += (int64_t)gridDim.x * kBT) {
+        const int64_t r = base + tid;
+        const RowState rs = unrank_tile(u, base, r, sh_range);
+        const double gr = rs.valid ? (double)g[r] : 0.0;
+        const double pr = rs.valid ? gr * (double)x[r] : 0.0;
+        P += pr;
+        sh_s[tid] = rs.s;
+        sh_g[tid] = gr;
+        sh_p[tid] = pr;
+        __syncthreads();
+        const int nrows = (int)min((int64_t)kBT, u.dim - base);
+#pragma unroll 2
+        for (int rr = lane; rr < nrows; rr += 32) {
+            const uint64_t s = sh_s[rr];
+            const double gq = sh_g[rr], pq = sh_p[rr];
+#pragma unroll
+            for (int j = 0; j < MBW; ++j) {
+                const uint64_t tb = s & mk[j];
+                if (tb != 0 && tb != mk[j]) {
+                    const int64_t c = rank_of(u, s ^ mk[j]);
+                    F[j] = fma(gq, (double)__ldg(x + c), F[j]);
+                    Fd[j] += pq;
                 }
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) acc[warp][b] += v;
         }
+        // the next tile overwrites the staged rows after unrank_tile's barrier
     }
+#pragma unroll
+    for (int j = 0; j < MBW; ++j)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            F[j] += __shfl_xor_sync(0xffffffffu, F[j], o);
+            Fd[j] += __shfl_xor_sync(0xffffffffu, Fd[j], o);
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) P += __shfl_xor_sync(0xffffffffu, P, o);
+    if (lane == 0) sh_red[warp] = P;
     __syncthreads();
-    for (int b = threadIdx.x; b < nbc; b += blockDim.x) {
-        double s = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) s += acc[w][b];
-        part[(size_t)blockIdx.x * nb + b0 + b] = s;
-    }
+    double Pb = 0.0;
+    for (int w = 0; w < kBT / 32; ++w) Pb += sh_red[w];
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < MBW; ++j) {
+            const int b = warp + 32 * j;
+            if (b < nbc) part[(size_t)blockIdx.x * nb + b0 + b] = 0.25 * (Pb - 2.0 * Fd[j]) + 0.5 * F[j];
+        }
 }
 
 // out[b] = sum_c part[c][b] in fixed order.
@@ -221,25 +257,36 @@ xd_status u1_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, int n
     }
 }
 
+template <typename T>
+static xd_status launch_bilinear_bp(const U1View &u, const uint64_t *masks, int nb, int grid, const void *g,
+                                    const void *x, double *part, cudaStream_t st) {
+    for (int b0 = 0; b0 < nb; b0 += kChunk) {
+        const int nbc = std::min(kChunk, nb - b0);
+        const int mbw = (nbc + 31) / 32;
+        auto go = [&](auto kern) {
+            kern<<<grid, kBT, 0, st>>>(u, masks, nb, b0, (const T *)g, (const T *)x, part);
+        };
+        if (mbw <= 1) go(k_bilinear_bp<T, 1>);
+        else if (mbw <= 2) go(k_bilinear_bp<T, 2>);
+        else if (mbw <= 4) go(k_bilinear_bp<T, 4>);
+        else go(k_bilinear_bp<T, 8>);
+        XD_CUDA(cudaGetLastError());
+    }
+    return XD_OK;
+}
+
 xd_status u1_bilinear(const xd_ham_s *h, const void *g, const void *x, xd_dtype dt, double *dJ,
                       cudaStream_t st) {
     const xd_basis_s *b = h->b;
     const int nb = b->nb;
     const U1View u = b->u1view();
-    const int grid = grid_for(u.dim, kThreads, 4);
+    const int grid = grid_for(u.dim, kBT, 1);
     xd_ham_s *hm = const_cast<xd_ham_s *>(h);
     XD_TRY(ensure_partials(hm, sizeof(double) * (size_t)grid * nb));
     const uint64_t *d_masks = (const uint64_t *)(h->d_bond + nb);
     double *d_part = hm->d_part;
-    for (int b0 = 0; b0 < nb; b0 += kChunk) {
-        if (dt == XD_F64)
-            k_bilinear<double><<<grid, kThreads, 0, st>>>(u, d_masks, nb, b0, (const double *)g,
-                                                          (const double *)x, d_part);
-        else
-            k_bilinear<float><<<grid, kThreads, 0, st>>>(u, d_masks, nb, b0, (const float *)g,
-                                                         (const float *)x, d_part);
-        XD_CUDA(cudaGetLastError());
-    }
+    if (dt == XD_F64) XD_TRY(launch_bilinear_bp<double>(u, d_masks, nb, grid, g, x, d_part, st));
+    else XD_TRY(launch_bilinear_bp<float>(u, d_masks, nb, grid, g, x, d_part, st));
     k_sum_columns<<<(nb + 127) / 128, 128, 0, st>>>(d_part, grid, nb, dJ);
     XD_CUDA(cudaGetLastError());
     return XD_OK;
@@ -323,18 +370,11 @@ extern "C" xd_status xd_apply_bilinear_noalloc(xd_ham h, const void *g, const vo
     double *part = nullptr;
     XD_TRY(noalloc_scratch(&part));
     const U1View u = b->u1view();
-    const int grid = std::min(grid_for(u.dim, kThreads, 4), kNoAllocCtas);
+    const int grid = std::min(grid_for(u.dim, kBT, 1), kNoAllocCtas);
     const uint64_t *masks = (const uint64_t *)(h->d_bond + nb);
     cudaStream_t st = (cudaStream_t)stream;
-    for (int b0 = 0; b0 < nb; b0 += kChunk) {
-        if (dt == XD_F64)
-            k_bilinear<double><<<grid, kThreads, 0, st>>>(u, masks, nb, b0, (const double *)g,
-                                                          (const double *)x, part);
-        else
-            k_bilinear<float><<<grid, kThreads, 0, st>>>(u, masks, nb, b0, (const float *)g,
-                                                         (const float *)x, part);
-        XD_CUDA(cudaGetLastError());
-    }
+    if (dt == XD_F64) XD_TRY(launch_bilinear_bp<double>(u, masks, nb, grid, g, x, part, st));
+    else XD_TRY(launch_bilinear_bp<float>(u, masks, nb, grid, g, x, part, st));
     k_sum_columns<<<(nb + 127) / 128, 128, 0, st>>>(part, grid, nb, dJ);
     XD_CUDA(cudaGetLastError());
     return XD_OK;

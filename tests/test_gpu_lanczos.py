@@ -59,9 +59,12 @@ def test_ground_state_vector_and_residual(orc):
 
 def test_bilinear_matches_oracle(orc):
     A = api()
-    for N, nup, seed in [(10, 5, 1), (13, 6, 2), (16, 8, 3)]:
-        bonds = W.random_bonds(N, 2 * N, seed)
-        J = W.uniform_couplings(2 * N, seed)
+    # bond counts cover one to eight bonds per warp and two launches of 256
+    # bonds; dimensions span one to many row tiles of 1024
+    for N, nup, nb, seed in [(10, 5, 20, 1), (13, 6, 26, 2), (16, 8, 32, 3), (18, 9, 100, 4),
+                             (14, 7, 91, 6), (24, 2, 270, 5)]:
+        bonds = W.random_bonds(N, nb, seed)
+        J = W.uniform_couplings(nb, seed)
         st = orc.enumerate_states(N, nup)
         ham = A.Hamiltonian(A.Basis(N, nup, bonds), J)
         g, x = orc.rng_normal(seed, 0, st.size), orc.rng_normal(seed + 9, 0, st.size)
@@ -71,6 +74,11 @@ def test_bilinear_matches_oracle(orc):
         # deterministic: same call, same bits
         dJ2 = ham.bilinear(torch.from_numpy(g).cuda(), torch.from_numpy(x).cuda()).cpu().numpy()
         assert np.array_equal(dJ, dJ2)
+        # FP32 vectors: the sums run in FP64 on the float values
+        g32, x32 = g.astype(np.float32), x.astype(np.float32)
+        dJ32 = ham.bilinear(torch.from_numpy(g32).cuda(), torch.from_numpy(x32).cuda()).cpu().numpy()
+        ref32 = orc.bond_forms(N, st, bonds, g32.astype(np.float64), x32.astype(np.float64))
+        assert rel_l2(dJ32, ref32) <= 1e-12
 
 
 def test_autograd_apply(orc):
