@@ -64,8 +64,11 @@ struct SpParams {
     float jcross;               // sum over cross bonds of J/4
 };
 
+constexpr int kPB = 16;  // prefix bonds per step of the prefix streams
+__host__ __device__ inline int pad_pa(int maxpa) { return (maxpa + kPB - 1) / kPB * kPB; }
+
 struct SpSmem {
-    size_t xs, nb, jh, pc, pl, cmeta, cc, rqm, noff, nn, total;
+    size_t xs, nb, jh, pc, pl, plc, cmeta, cc, rqm, noff, nn, total;
     __host__ __device__ SpSmem(const SpParams &p, int maxblk) {
         size_t o = 0;
         auto al = [&](size_t a) { o = (o + a - 1) / a * a; };
@@ -83,6 +86,9 @@ struct SpSmem {
         al(16);
         pl = o;
         o += (size_t)kB * p.maxpa * sizeof(uint64_t);
+        al(16);
+        plc = o;  // coefficients of the listed bonds, zero-padded to kPB
+        o += (size_t)kB * pad_pa(p.maxpa) * sizeof(float);
         al(16);
         cmeta = o;
         o += (size_t)p.ncross * sizeof(uint32_t);
@@ -145,6 +151,8 @@ __global__ void __launch_bounds__(kT, 2) k_spmm(SpParams p, const float *__restr
     float *jh = (float *)(smem + lay.jh);
     float *pc = (float *)(smem + lay.pc);
     uint64_t *pl = (uint64_t *)(smem + lay.pl);
+    float *plc = (float *)(smem + lay.plc);
+    const int mpc = pad_pa(p.maxpa);
     uint32_t *cmeta = (uint32_t *)(smem + lay.cmeta);  // postfix site j | slot << 8
     float *cc = (float *)(smem + lay.cc);              // J/2 of each cross bond
     uint32_t *rqm = (uint32_t *)(smem + lay.rqm);      // per site: bit k = row bit that flips block k
@@ -196,7 +204,11 @@ __global__ void __launch_bounds__(kT, 2) k_spmm(SpParams p, const float *__restr
             if (h != kEmpty) {
                 const int64_t c0 = __ldg(p.pcsr_off + h), c1 = __ldg(p.pcsr_off + h + 1);
                 cnt = (int)(c1 - c0);
-                for (int q = lane; q < cnt; q += 32) pl[k * p.maxpa + q] = __ldg(p.pcsr + c0 + q);
+                for (int q = lane; q < pad_pa(cnt); q += 32) {
+                    const uint64_t ev = q < cnt ? __ldg(p.pcsr + c0 + q) : 0ull;
+                    if (q < cnt) pl[k * p.maxpa + q] = ev;
+                    plc[k * mpc + q] = q < cnt ? jh[(uint32_t)(ev & 4095u)] : 0.f;
+                }
                 for (int q = lane; q < p.npre; q += 32) {
                     const int a = p.pre[3 * q], b = p.pre[3 * q + 1];
                     const float j4 = 0.5f * jh[p.pre[3 * q + 2]];
@@ -270,26 +282,25 @@ __global__ void __launch_bounds__(kT, 2) k_spmm(SpParams p, const float *__restr
         };
         if (p.ncsite > 0) stage_site(0, nbuf);
         // prefix bonds: per block, coalesced streams from its neighbour blocks.
-        // Both rows of a thread load each neighbour, so that sixteen loads
-        // are in flight per thread before their uses: far neighbour blocks
-        // come from DRAM and only memory-level parallelism hides that latency.
+        // Both rows of a thread load each of kPB neighbours before any use
+        // (32 loads in flight per thread; the coefficients wait in shared
+        // memory): far neighbour blocks come from DRAM and only memory-level
+        // parallelism hides that latency.
 #pragma unroll
         for (int k = 0; k < kB; ++k) {
             const int npa = sh_npa[k];
             const uint64_t *e = pl + k * p.maxpa;
+            const float *cf = plc + k * mpc;
             float a[K];
 #pragma unroll
             for (int r = 0; r < K; ++r) a[r] = 0.f;
 #pragma unroll 1
-            for (int q0 = 0; q0 < npa; q0 += 8) {
-                float v[K][8];
-                float c[8];
+            for (int q0 = 0; q0 < npa; q0 += kPB) {
+                float v[K][kPB];
 #pragma unroll
-                for (int w = 0; w < 8; ++w) {
+                for (int w = 0; w < kPB; ++w) {
                     const bool ok = q0 + w < npa;
-                    const uint64_t ev = ok ? e[q0 + w] : 0ull;
-                    c[w] = ok ? jh[(uint32_t)(ev & 4095u)] : 0.f;
-                    const float *src = x + (int64_t)(ev >> 12);
+                    const float *src = x + (ok ? (int64_t)(e[q0 + w] >> 12) : 0);
 #pragma unroll
                     for (int r = 0; r < K; ++r) {
                         const int i = tid + r * kT;
@@ -297,9 +308,11 @@ __global__ void __launch_bounds__(kT, 2) k_spmm(SpParams p, const float *__restr
                     }
                 }
 #pragma unroll
-                for (int w = 0; w < 8; ++w)
+                for (int w = 0; w < kPB; ++w) {
+                    const float c = cf[q0 + w];
 #pragma unroll
-                    for (int r = 0; r < K; ++r) a[r] = fmaf(c[w], v[r][w], a[r]);
+                    for (int r = 0; r < K; ++r) a[r] = fmaf(c, v[r][w], a[r]);
+                }
             }
 #pragma unroll
             for (int r = 0; r < K; ++r) acc[r][k] += a[r];
