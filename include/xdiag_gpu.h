@@ -84,7 +84,7 @@ typedef struct xd_ham_s *xd_ham;
  * interaction graph `bonds` ([nb][2] site pairs, 0-based, i != j, host
  * memory).  sym == NULL gives the U(1) block.  The graph decides the index
  * layout; its couplings are set by xd_ham_create.
- * Limits: 2 <= N <= 40 for U(1) blocks, N <= 40 and ngroup <= 64 for
+ * Limits: 2 <= N <= 40 for U(1) blocks, N <= 40 and ngroup <= 128 for
  * symmetric ones, 1 <= nb <= 4096, dim < 2^40.  Errors: XD_EINVAL,
  * XD_ERANGE, XD_ESYM, XD_ENOMEM, XD_ECUDA. */
 xd_status xd_basis_create(int N, int nup, const int32_t *bonds, int nb,

@@ -28,7 +28,7 @@ xd_status cuda_status(cudaError_t e, const char *what);
     } while (0)
 
 constexpr int kMaxBonds = 4096;
-constexpr int kMaxGroup = 64;
+constexpr int kMaxGroup = 128;
 constexpr int kMaxN = 40;
 
 // ----------------------------------------------------- U(1) index layout

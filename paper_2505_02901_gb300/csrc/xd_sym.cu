@@ -586,6 +586,16 @@ xd_status sym_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, cuda
     XD_TRY(sym_work(h, 0, &w));
     const SymView v = b->symview();
     size_t smem = (size_t)nb * 16 + 2 * G * sizeof(double) + (size_t)(G + 1) * (G + 1) * sizeof(double);
+    {
+        int dev = 0, optin = 0;
+        XD_CUDA(cudaGetDevice(&dev));
+        XD_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (smem > (size_t)optin) {
+            set_error("symmetric product: %d bonds and %d group elements need %zu bytes of shared memory",
+                      nb, G, smem);
+            return XD_ERANGE;
+        }
+    }
     int grid = grid_for(v.dim, kThreads, 8);
     if (dt == XD_C128) {
         auto kern = k_sym_apply<true>;

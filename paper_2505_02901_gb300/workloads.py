@@ -88,6 +88,42 @@ def chain_translations(N: int) -> np.ndarray:
     return np.array([[(i + n) % N for i in range(N)] for n in range(N)], dtype=np.int32)
 
 
+def chain_dihedral(N: int) -> np.ndarray:
+    """The dihedral group D_N of the periodic chain: perms[n][i] = (i + n) mod N
+    (translations T^n), then perms[N + n][i] = (n - i) mod N (reflections)."""
+    rot = [[(i + n) % N for i in range(N)] for n in range(N)]
+    ref = [[(n - i) % N for i in range(N)] for n in range(N)]
+    return np.array(rot + ref, dtype=np.int32)
+
+
+def chain_dihedral_characters(N: int, m: int, parity: int) -> np.ndarray:
+    """One-dimensional characters of D_N (Sec. 3.9.2): momentum k = 2 pi m / N
+    with k in {0, pi}, chi(T^n) = exp(i k n), chi(reflection n) = parity exp(i k n)."""
+    if (2 * m) % N != 0 or parity not in (1, -1):
+        raise ValueError("D_N has one-dimensional irreps only at k = 0, pi and parity +-1")
+    k = 2 * math.pi * m / N
+    rot = [cmath.exp(1j * k * n) for n in range(N)]
+    return np.array(rot + [parity * z for z in rot], dtype=np.complex128)
+
+
+def torus_space_group(L: int) -> np.ndarray:
+    """Space group of the periodic L x L square lattice: the 8 point operations
+    of the square (rotations by 90 degrees and mirrors) followed by the L^2
+    translations, perms[g][i] = site of op(x, y) + (a, b), 8 L^2 elements."""
+    ops = [lambda x, y: (x, y), lambda x, y: (-y, x), lambda x, y: (-x, -y), lambda x, y: (y, -x),
+           lambda x, y: (-x, y), lambda x, y: (x, -y), lambda x, y: (y, x), lambda x, y: (-y, -x)]
+    out = []
+    for op in ops:
+        for b in range(L):
+            for a in range(L):
+                row = []
+                for i in range(L * L):
+                    x, y = op(i % L, i // L)
+                    row.append((x + a) % L + L * ((y + b) % L))
+                out.append(row)
+    return np.array(out, dtype=np.int32)
+
+
 def torus_translations(Lx: int, Ly: int) -> np.ndarray:
     """perms[a + Lx*b][i] = site of (x+a, y+b) for i = (x, y)."""
     out = []

@@ -20,8 +20,21 @@ def _torus(Lx, Ly, mx, my):
     return Lx * Ly, b, J, W.torus_translations(Lx, Ly), W.torus_characters(Lx, Ly, mx, my)
 
 
+def _dihedral(N, m, parity):
+    return N, W.chain(N), np.ones(N), W.chain_dihedral(N), W.chain_dihedral_characters(N, m, parity)
+
+
+def _space_group(L):
+    # 8 L^2 group elements: 128 at L = 4, the largest group the library takes
+    b, J = W.square_j1j2(L, L)
+    g = W.torus_space_group(L)
+    return L * L, b, J, g, np.ones(len(g), dtype=np.complex128)
+
+
 CASES = [_chain(8, 0), _chain(8, 4), _chain(10, 1), _chain(12, 3), _chain(13, 2),
-         _torus(3, 3, 1, 0), _torus(4, 4, 0, 0), _torus(4, 4, 1, 2), _torus(2, 6, 1, 1)]
+         _torus(3, 3, 1, 0), _torus(4, 4, 0, 0), _torus(4, 4, 1, 2), _torus(2, 6, 1, 1),
+         _dihedral(8, 0, 1), _dihedral(10, 5, -1), _dihedral(12, 0, -1), _dihedral(12, 6, 1),
+         _space_group(4)]
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))

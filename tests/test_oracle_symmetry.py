@@ -125,3 +125,65 @@ def test_burnside_6x6_momentum_sectors(orc):
     total = sum(orc.burnside_dim(36, 18, perms, W.torus_characters(6, 6, mx, my))
                 for mx in range(6) for my in range(6))
     assert total == math.comb(36, 18)
+
+
+@pytest.mark.parametrize("N", [8, 10])
+def test_dihedral_blocks(orc, N):
+    """D_N (translations and reflections): every one-dimensional irrep block is
+    the projection of H, and its spectrum lies inside the U(1) spectrum."""
+    bonds, J, perms = W.chain(N), np.ones(N), W.chain_dihedral(N)
+    nup = N // 2
+    st = orc.enumerate_states(N, nup)
+    H = orc.dense_u1(N, st, bonds, J)
+    ev = np.linalg.eigvalsh(H)
+    total = 0
+    for m in (0, N // 2):
+        for parity in (1, -1):
+            chi = W.chain_dihedral_characters(N, m, parity)
+            blk = orc.SymBlock(N, nup, perms, chi)
+            assert blk.dim == orc.burnside_dim(N, nup, perms, chi)
+            total += blk.dim
+            if blk.dim == 0:
+                continue
+            B = blk.lift(st)
+            assert np.abs(B.conj().T @ B - np.eye(blk.dim)).max() < 1e-13
+            Hk = blk.dense(bonds, J)
+            assert np.abs(Hk - B.conj().T @ H @ B).max() < 1e-13
+            for e in np.linalg.eigvalsh(Hk):
+                assert np.abs(ev - e).min() < 1e-11
+    # the one-dimensional irreps do not exhaust the block (D_N has 2-d irreps)
+    assert 0 < total < math.comb(N, nup)
+
+
+def test_space_group_4x4_block(orc):
+    """The 128-element space group of the 4x4 square lattice, trivial irrep:
+    the block's product equals the projected U(1) product on random vectors,
+    and its lowest level is the ground state of the whole Sz = 0 block."""
+    from scipy.sparse.linalg import LinearOperator, eigsh
+    bonds, J = W.square_j1j2(4, 4)
+    perms = W.torus_space_group(4)
+    chi = np.ones(len(perms), dtype=np.complex128)
+    st = orc.enumerate_states(16, 8)
+    blk = orc.SymBlock(16, 8, perms, chi)
+    assert blk.dim == orc.burnside_dim(16, 8, perms, chi)
+    B = blk.lift(st)
+    assert np.abs(B.conj().T @ B - np.eye(blk.dim)).max() < 1e-13
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        x = rng.standard_normal(blk.dim)
+        hx = B.conj().T @ orc.apply_u1(16, st, bonds, J, (B @ x).real)
+        assert np.abs(blk.apply(bonds, J, x) - hx).max() < 1e-12
+    op = LinearOperator((st.size, st.size), matvec=lambda v: orc.apply_u1(16, st, bonds, J, v))
+    e0 = eigsh(op, k=1, which="SA", tol=1e-12)[0][0]
+    # the ground state of the frustrated 4x4 J1-J2 model (J2 = 0.5) is fully symmetric
+    assert abs(np.linalg.eigvalsh(blk.dense(bonds, J))[0] - e0) < 1e-9
+
+
+def test_dihedral_chain36_dimension(orc):
+    """N = 36 chain, Sz = 0, translations and reflections, trivial irrep: the
+    sector of the paper's U(1) + lattice benchmark, quoted there as dim 1.3e8."""
+    perms = W.chain_dihedral(36)
+    chi = W.chain_dihedral_characters(36, 0, 1)
+    d = orc.burnside_dim(36, 18, perms, chi)
+    assert d == 126068558
+    assert abs(d - 1.3e8) / 1.3e8 < 0.05
