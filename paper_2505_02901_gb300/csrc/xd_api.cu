@@ -218,6 +218,7 @@ static void free_basis(xd_basis_s *b) {
     cudaFree(b->d_minrot);
     cudaFree(b->d_amask);
     cudaFree(b->d_tg);
+    cudaFree(b->d_cg);
     cudaFree(b->d_chi);
     delete b;
 }
@@ -255,6 +256,9 @@ xd::SymView xd_basis_s::symview() const {
     v.minrot = d_minrot;
     v.amask = d_amask;
     v.tg = d_tg;
+    v.cn = cn;
+    v.cdih = cdih;
+    v.cg = d_cg;
     return v;
 }
 

@@ -69,6 +69,11 @@ struct SymView {
     int tx, ty;
     const uint8_t *minrot, *amask;
     const int16_t *tg;
+    // rotations of a ring (i -> i + n mod N), with or without the reflections
+    // (i -> n - i mod N), when detected: cn = N (0 otherwise), cdih = 1 with
+    // reflections; cg[n] = group index of rotation n, cg[N + n] of reflection n
+    int cn, cdih;
+    const int16_t *cg;
 };
 
 struct Bond {
@@ -130,6 +135,8 @@ struct xd_basis_s {
     int tx = 0, ty = 0;              // detected torus translation group
     uint8_t *d_minrot = nullptr, *d_amask = nullptr;
     int16_t *d_tg = nullptr;
+    int cn = 0, cdih = 0;            // detected ring rotations (+ reflections)
+    int16_t *d_cg = nullptr;
     double *d_chi = nullptr;  // [G][2]
     xd::BlockLayoutHost blk;
     xd::SpmmLayoutHost spmm;

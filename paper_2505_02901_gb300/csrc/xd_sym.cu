@@ -109,8 +109,66 @@ __device__ __forceinline__ Orbit orbit_min_torus(const SymView &v, uint64_t s) {
     return o;
 }
 
+// Ring rotations T_n (i -> i + n mod N) and reflections R_n (i -> n - i mod
+// N): T_n s = rotr(s, n) and R_n s = rotr(rev(s), N - 1 - n) on N-bit words.
+// The smallest image has the longest run of zeros at its top, so only the
+// rotations that bring a longest cyclic zero run of the word there are
+// evaluated: z & rotr(z, 1) & ... & rotr(z, L - 1) marks the starts q of the
+// runs of length >= L (z = zero bits of the word), and the run starting at q
+// reaches the top under rotr(., (q + L) mod N).
+__device__ __forceinline__ uint64_t ring_rotr(uint64_t w, int j, int N, uint64_t mask) {
+    return j == 0 ? w : (((w >> j) | (w << (N - j))) & mask);
+}
+
+__device__ __forceinline__ Orbit orbit_min_ring(const SymView &v, uint64_t s) {
+    const int N = v.cn;
+    const uint64_t mask = N == 64 ? ~0ull : ((1ull << N) - 1);
+    Orbit o{~0ull, 0, 0};
+    for (int refl = 0; refl <= v.cdih; ++refl) {
+        const uint64_t w = refl ? (__brevll(s) >> (64 - N)) : s;
+        const uint64_t z = ~w & mask;
+        if (z == 0) {  // all ones: every element fixes the word
+            o.rep = w;
+            o.u = __ldg(v.cg);
+            o.cnt = v.G;
+            return o;
+        }
+        uint64_t r = z;
+        int L = 1;
+        while (L < N) {
+            const uint64_t r2 = r & ring_rotr(z, L, N, mask);
+            if (!r2) break;
+            r = r2;
+            ++L;
+        }
+        while (r) {
+            const int q = __ffsll((long long)r) - 1;
+            r &= r - 1;
+            int n = q + L;
+            if (n >= N) n -= N;
+            const uint64_t img = ring_rotr(w, n, N, mask);
+            if (img <= o.rep) {
+                int m = n;
+                if (refl) {
+                    m = N - 1 - n;
+                    if (m < 0) m += N;
+                }
+                const int g = __ldg(v.cg + refl * N + m);
+                if (img < o.rep) {
+                    o.rep = img;
+                    o.u = g;
+                    o.cnt = 1;
+                } else {
+                    ++o.cnt;
+                }
+            }
+        }
+    }
+    return o;
+}
+
 __device__ __forceinline__ Orbit orbit_min(const SymView &v, uint64_t s) {
-    return v.tx ? orbit_min_torus(v, s) : orbit_min_tables(v, s);
+    return v.tx ? orbit_min_torus(v, s) : v.cn ? orbit_min_ring(v, s) : orbit_min_tables(v, s);
 }
 
 __device__ __forceinline__ uint64_t find_block(const int64_t *__restrict__ hi_off, uint64_t lo,
@@ -471,6 +529,35 @@ static xd_status make_tables(xd_basis_s *b) {
         XD_CUDA(cudaMemcpy(b->d_tg, tg.data(), tg.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
         b->tx = Lx;
         b->ty = Ly;
+    }
+    // rotations of a ring, with or without its reflections?
+    if (!b->tx && N <= 64 && (G == N || G == 2 * N)) {
+        std::vector<int16_t> cg(2 * N, -1);
+        bool ok = true;
+        for (int g = 0; g < G && ok; ++g) {
+            const int32_t *p = b->perms.data() + (size_t)g * N;
+            const int n = p[0];
+            bool rot = true, ref = true;
+            for (int i = 0; i < N; ++i) {
+                rot = rot && p[i] == (i + n) % N;
+                ref = ref && p[i] == ((n - i) % N + N) % N;
+            }
+            if (N > 2 && rot && ref) ok = false;  // only the identity of N <= 2 is both
+            const int slot = rot ? n : ref ? N + n : -1;
+            if (slot < 0 || cg[slot] >= 0) ok = false;
+            else cg[slot] = (int16_t)g;
+        }
+        int nrot = 0, nref = 0;
+        for (int n = 0; n < N; ++n) {
+            nrot += cg[n] >= 0;
+            nref += cg[N + n] >= 0;
+        }
+        if (ok && nrot == N && (nref == 0 || nref == N) && N + nref == G) {
+            XD_CUDA(cudaMalloc((void **)&b->d_cg, cg.size() * sizeof(int16_t)));
+            XD_CUDA(cudaMemcpy(b->d_cg, cg.data(), cg.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
+            b->cn = N;
+            b->cdih = nref ? 1 : 0;
+        }
     }
     XD_CUDA(cudaMalloc((void **)&b->d_act, tab.size() * sizeof(uint64_t)));
     XD_CUDA(cudaMemcpy(b->d_act, tab.data(), tab.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
