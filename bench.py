@@ -180,9 +180,9 @@ def extra_rows(hbm):
     bilinear forms (14-rung ladder, FP64), symmetric products (6x6 J1-J2,
     k=(0,0) FP64 and k=(pi/3,0) complex128), the 6x6 U(1) product in FP32
     (dim 9,075,135,300), the paper's N=36 chain U(1) benchmark (product and
-    steady-state Lanczos iteration, FP64 and FP32 storage), its N=36 chain
-    U(1) + lattice benchmark (translations and reflections) and the N=16
-    chain Lanczos.  Fractions are
+    steady-state Lanczos iteration, FP64 and FP32 storage), its N=36 and
+    N=40 chain U(1) + lattice benchmarks (translations and reflections) and
+    the N=16 chain Lanczos.  Fractions are
     compulsory bytes (vectors read and written once) over time, of the
     measured HBM bandwidth."""
     import torch
@@ -270,21 +270,23 @@ def extra_rows(hbm):
     # The paper's U(1) + lattice Lanczos benchmark at N=36: the chain with its
     # translations and reflections (D_36), fully symmetric irrep (dim
     # 126,068,558, quoted as 1.3e8), one iteration 7.60 s in FP64 on 64 threads.
-    t0 = time.perf_counter()
-    basis = api.Basis(36, 18, W.chain(36),
-                      symmetry=(W.chain_dihedral(36), W.chain_dihedral_characters(36, 0, 1)))
-    build_s = time.perf_counter() - t0
-    h = api.Hamiltonian(basis, [1.0] * 36)
-    x = torch.randn(basis.dim, dtype=torch.float64, device="cuda")
-    y = torch.empty_like(x)
-    ms = _event_time(lambda: h.apply(x, out=y), reps=2)
-    del x, y
-    torch.cuda.empty_cache()
-    row("paper_chain36_lattice_f64", ms, (2 * 8 + 9) * basis.dim, dim=basis.dim, group=72,
-        basis_build_s=build_s, lanczos_s_per_iter=_lanczos_steady(h, torch.float64, 4),
-        paper_fp64_s_per_iter=7.60, paper_hardware="64 OpenMP threads, Xeon Platinum 8360Y")
-    del basis, h
-    torch.cuda.empty_cache()
+    # The same at N=40 (dim 1,723,176,308, quoted as 1.7e9): 131 s per iteration.
+    for Nc, paper_s in ((36, 7.60), (40, 131.0)):
+        t0 = time.perf_counter()
+        basis = api.Basis(Nc, Nc // 2, W.chain(Nc),
+                          symmetry=(W.chain_dihedral(Nc), W.chain_dihedral_characters(Nc, 0, 1)))
+        build_s = time.perf_counter() - t0
+        h = api.Hamiltonian(basis, [1.0] * Nc)
+        x = torch.randn(basis.dim, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(x)
+        ms = _event_time(lambda: h.apply(x, out=y), reps=2)
+        del x, y
+        torch.cuda.empty_cache()
+        row(f"paper_chain{Nc}_lattice_f64", ms, (2 * 8 + 9) * basis.dim, dim=basis.dim, group=2 * Nc,
+            basis_build_s=build_s, lanczos_s_per_iter=_lanczos_steady(h, torch.float64, 3),
+            paper_fp64_s_per_iter=paper_s, paper_hardware="64 OpenMP threads, Xeon Platinum 8360Y")
+        del basis, h
+        torch.cuda.empty_cache()
     # a6/a7: chain N=16 Lanczos, 100 steps
     h = api.Hamiltonian(api.Basis(16, 8, W.chain(16)), [1.0] * 16)
     h.lanczos(max_iter=100, seed=1)

@@ -187,3 +187,7 @@ def test_dihedral_chain36_dimension(orc):
     d = orc.burnside_dim(36, 18, perms, chi)
     assert d == 126068558
     assert abs(d - 1.3e8) / 1.3e8 < 0.05
+    # N = 40, quoted as dim 1.7e9
+    d40 = orc.burnside_dim(40, 20, W.chain_dihedral(40), W.chain_dihedral_characters(40, 0, 1))
+    assert d40 == 1723176308
+    assert abs(d40 - 1.7e9) / 1.7e9 < 0.05
