@@ -73,6 +73,7 @@ def _declare(L):
         "xo_apply_rows_rng": (None, [_i32, _i32, _i32, _i32p, _f64p, _u64, _i64p, _i64, _f64p]),
         "xo_flip_index_rows": (None, [_i32, _i32, _i32, _i32p, _i64p, _i64, _i64p]),
         "xo_bond_forms": (None, [_i32, _u64p, _i64, _i32, _i32p, _f64p, _f64p, _f64p]),
+        "xo_correlations": (None, [_i32, _u64p, _i64, _i32, _i32p, _i32, _f64p, _f64p]),
         "xo_act": (_u64, [_i32, _i32p, _u64]),
         "xo_group_check": (_i32, [_i32, _i32, _i32p, _f64p, _f64p]),
         "xo_rep": (_u64, [_i32, _i32, _i32p, _u64, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
@@ -177,6 +178,17 @@ def bond_forms(N: int, states: np.ndarray, bonds, g: np.ndarray, x: np.ndarray) 
     out = np.empty(nb, dtype=np.float64)
     lib().xo_bond_forms(N, _p(states, _u64p), states.size, nb, _p(b, _i32p), _p(g, _f64p),
                         _p(x, _f64p), _p(out, _f64p))
+    return out
+
+
+def correlations(N: int, states: np.ndarray, pairs, kind: str, psi: np.ndarray) -> np.ndarray:
+    """out[p] = <psi| O_{i_p j_p} |psi>, O = Sz_i Sz_j (kind "zz") or S_i.S_j
+    (kind "ss"); i = j allowed."""
+    b, n = _bonds(pairs)
+    psi = _f64(psi)
+    out = np.empty(n, dtype=np.float64)
+    lib().xo_correlations(N, _p(states, _u64p), states.size, n, _p(b, _i32p),
+                          {"zz": 0, "ss": 1}[kind], _p(psi, _f64p), _p(out, _f64p))
     return out
 
 

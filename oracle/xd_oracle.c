@@ -232,6 +232,39 @@ void xo_bond_forms(int N, const uint64_t *states, int64_t dim, int nb,
     }
 }
 
+/* Two-point spin correlations <psi| O_ij |psi> of a U(1) state (the inner
+ * product of Sec. 3.7 with the SzSz and SdotS operators of App. A on any site
+ * pair).  kind 0: O = Sz_i Sz_j, +1/4 for equal spins and -1/4 for opposite
+ * ones; kind 1: O = S_i.S_j, which adds (S+_i S-_j + S-_i S+_j)/2, taking a
+ * state with opposite spins to the one with both flipped.  For i = j the
+ * operators are (Sz_i)^2 = 1/4 and S_i.S_i = 3/4 (S(S+1) with S = 1/2). */
+void xo_correlations(int N, const uint64_t *states, int64_t dim, int npairs,
+                     const int32_t *pairs, int kind, const double *psi,
+                     double *out)
+{
+    (void)N;
+    for (int p = 0; p < npairs; ++p) {
+        int i = pairs[2 * p], j = pairs[2 * p + 1];
+        double acc = 0.0;
+        for (int64_t r = 0; r < dim; ++r) {
+            uint64_t s = states[r];
+            double w = psi[r] * psi[r];
+            if (i == j) {
+                acc += (kind ? 0.75 : 0.25) * w;
+            } else if (bit(s, i) == bit(s, j)) {
+                acc += 0.25 * w;
+            } else {
+                acc -= 0.25 * w;
+                if (kind) {
+                    uint64_t t = s ^ ((uint64_t)1 << i) ^ ((uint64_t)1 << j);
+                    acc += 0.5 * psi[r] * psi[xo_index_search(states, dim, t)];
+                }
+            }
+        }
+        out[p] = acc;
+    }
+}
+
 /* ------------------------------------------------------------- symmetry */
 
 /* (g s)_i = s_{g(i)} (Sec. 3.10). */

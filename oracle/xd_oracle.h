@@ -23,6 +23,9 @@ void xo_flip_index_rows(int N, int nup, int nb, const int32_t *bonds,
 void xo_bond_forms(int N, const uint64_t *states, int64_t dim, int nb,
                    const int32_t *bonds, const double *g, const double *x,
                    double *out);
+void xo_correlations(int N, const uint64_t *states, int64_t dim, int npairs,
+                     const int32_t *pairs, int kind, const double *psi,
+                     double *out);
 uint64_t xo_act(int N, const int32_t *perm, uint64_t s);
 int xo_group_check(int N, int G, const int32_t *perms, const double *chi_re,
                    const double *chi_im);
