@@ -185,6 +185,7 @@ def extra_rows(hbm):
     the N=16 chain Lanczos.  Fractions are
     compulsory bytes (vectors read and written once) over time, of the
     measured HBM bandwidth."""
+    import numpy as np
     import torch
 
     from paper_2505_02901_gb300 import api, workloads as W
@@ -225,6 +226,25 @@ def extra_rows(hbm):
     ms = _event_time(lambda: h.apply(x))
     row("a5_apply_ladder28_f64", ms, 2 * 8 * h.dim, elems(28, 14, 56))
     del h, g, x
+    torch.cuda.empty_cache()
+    # next row 1: eigenvector and observables -- ground state of the N=28
+    # chain (two Lanczos passes, FP64) and its <S0.Sj>, <Sz0 Szj> for all j
+    hc = api.Hamiltonian(api.Basis(28, 14, W.chain(28)), [1.0] * 28)
+    t0 = time.perf_counter()
+    e0, psi, info = hc.ground_state(max_iter=150, seed=SEED)
+    gs_s = time.perf_counter() - t0
+    pairs = [(0, j) for j in range(28)]
+    t0 = time.perf_counter()
+    ss = hc.basis.correlations(psi, pairs, "ss")
+    ss_ms = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    zz = hc.basis.correlations(psi, pairs, "zz")
+    zz_ms = (time.perf_counter() - t0) * 1e3
+    out["next1_correlations_chain28_f64"] = {
+        "ground_state_s": gs_s, "lanczos_steps": info["n_iter"], "e0": e0,
+        "ss_ms_28_pairs": ss_ms, "zz_ms_28_pairs": zz_ms, "s0s1_minus_e0_over_n": float(ss[1] - e0 / 28),
+        "su2_max_dev": float(np.abs(ss - 3 * zz).max()), "sum_rule": float(ss.sum())}
+    del hc, psi
     torch.cuda.empty_cache()
     # a4': symmetric 6x6 blocks
     b6, J6 = W.square_j1j2(6, 6)

@@ -153,6 +153,19 @@ xd_status xd_apply_bilinear(xd_ham h, const void *g, const void *x,
 xd_status xd_apply_bilinear_noalloc(xd_ham h, const void *g, const void *x,
                                     xd_dtype dtype, double *dJ, xd_stream stream);
 
+/* Two-point spin correlations of a state on a U(1) block (the expectation
+ * values of Sec. 3.7 inner, with the SzSz / SdotS operators of App. A on
+ * arbitrary site pairs): out[p] = <psi| O |psi> for pair p = (i_p, j_p),
+ * O = Sz_i Sz_j (kind 0) or S_i.S_j (kind 1); i = j is allowed ((Sz_i)^2 =
+ * 1/4, S_i.S_i = 3/4 times <psi|psi>).  psi is not normalised by the call.
+ * psi: device [dim] vector of dtype XD_F64 or XD_F32; pairs: host
+ * [npairs][2] site indices in [0, N); out: host [npairs] doubles.  Sums run
+ * in FP64 in a fixed order (deterministic).  Symmetry-adapted blocks are
+ * rejected (XD_EINVAL).  Synchronous; allocates its workspace per call. */
+xd_status xd_correlations(xd_basis b, const void *psi, xd_dtype dtype,
+                          const int32_t *pairs, int npairs, int kind,
+                          double *out);
+
 /* ---------------------------------------------------------------- Lanczos */
 
 /* Lanczos tridiagonalisation from the seeded normal start vector

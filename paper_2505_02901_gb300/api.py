@@ -85,6 +85,18 @@ class Basis:
         check(_lib.lib().xd_basis_index(self._h, int(s), ctypes.byref(i)))
         return int(i.value)
 
+    def correlations(self, psi: torch.Tensor, pairs, kind: str = "ss") -> np.ndarray:
+        """<psi| O_ij |psi> for every site pair, O = S_i.S_j (kind "ss") or
+        Sz_i Sz_j (kind "zz") (Sec. 3.7 inner); U(1) blocks."""
+        _check_vec(psi, self.dim, "psi")
+        p = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        out = np.zeros(p.shape[0])
+        torch.cuda.current_stream().synchronize()
+        check(_lib.lib().xd_correlations(self._h, _ptr(psi), _dtype_code(psi),
+                                         p.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), p.shape[0],
+                                         {"zz": 0, "ss": 1}[kind], out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and h.value and _lib._lib is not None:

@@ -142,7 +142,7 @@ constexpr int kChunk = 256;
 // in a fixed order (lane partials, a fixed shuffle tree, then the CTA
 // partial of each bond).  MBW = most bonds per warp.
 constexpr int kBT = 1024;
-template <typename T, int MBW>
+template <typename T, int MBW, bool ZZ>
 __global__ void __launch_bounds__(kBT) k_bilinear_bp(U1View u, const uint64_t *__restrict__ masks,
                                                      int nb, int b0, const T *__restrict__ g,
                                                      const T *__restrict__ x,
@@ -182,8 +182,10 @@ __global__ void __launch_bounds__(kBT) k_bilinear_bp(U1View u, const uint64_t *_
             for (int j = 0; j < MBW; ++j) {
                 const uint64_t tb = s & mk[j];
                 if (tb != 0 && tb != mk[j]) {
-                    const int64_t c = rank_of(u, s ^ mk[j]);
-                    F[j] = fma(gq, (double)__ldg(x + c), F[j]);
+                    if (!ZZ) {
+                        const int64_t c = rank_of(u, s ^ mk[j]);
+                        F[j] = fma(gq, (double)__ldg(x + c), F[j]);
+                    }
                     Fd[j] += pq;
                 }
             }
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(kBT) k_bilinear_bp(U1View u, const uint64_t *_
 #pragma unroll
         for (int j = 0; j < MBW; ++j) {
             const int b = warp + 32 * j;
-            if (b < nbc) part[(size_t)blockIdx.x * nb + b0 + b] = 0.25 * (Pb - 2.0 * Fd[j]) + 0.5 * F[j];
+            if (b < nbc) part[(size_t)blockIdx.x * nb + b0 + b] = 0.25 * (Pb - 2.0 * Fd[j]) + (ZZ ? 0.0 : 0.5 * F[j]);
         }
 }
 
@@ -257,7 +259,7 @@ xd_status u1_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, int n
     }
 }
 
-template <typename T>
+template <typename T, bool ZZ = false>
 static xd_status launch_bilinear_bp(const U1View &u, const uint64_t *masks, int nb, int grid, const void *g,
                                     const void *x, double *part, cudaStream_t st) {
     for (int b0 = 0; b0 < nb; b0 += kChunk) {
@@ -266,10 +268,10 @@ static xd_status launch_bilinear_bp(const U1View &u, const uint64_t *masks, int 
         auto go = [&](auto kern) {
             kern<<<grid, kBT, 0, st>>>(u, masks, nb, b0, (const T *)g, (const T *)x, part);
         };
-        if (mbw <= 1) go(k_bilinear_bp<T, 1>);
-        else if (mbw <= 2) go(k_bilinear_bp<T, 2>);
-        else if (mbw <= 4) go(k_bilinear_bp<T, 4>);
-        else go(k_bilinear_bp<T, 8>);
+        if (mbw <= 1) go(k_bilinear_bp<T, 1, ZZ>);
+        else if (mbw <= 2) go(k_bilinear_bp<T, 2, ZZ>);
+        else if (mbw <= 4) go(k_bilinear_bp<T, 4, ZZ>);
+        else go(k_bilinear_bp<T, 8, ZZ>);
         XD_CUDA(cudaGetLastError());
     }
     return XD_OK;
@@ -377,6 +379,81 @@ extern "C" xd_status xd_apply_bilinear_noalloc(xd_ham h, const void *g, const vo
     else XD_TRY(launch_bilinear_bp<float>(u, masks, nb, grid, g, x, part, st));
     k_sum_columns<<<(nb + 127) / 128, 128, 0, st>>>(part, grid, nb, dJ);
     XD_CUDA(cudaGetLastError());
+    return XD_OK;
+}
+
+// Two-point spin correlations out[p] = <psi| O_{i_p j_p} |psi> on a U(1)
+// block: the bilinear kernel with g = x = psi and the pair masks as bonds
+// (S_i.S_j), or its diagonal part alone (Sz_i Sz_j, no gathers).  A pair
+// with i = j has a one-bit mask that never flips: the kernel returns
+// <psi|psi>/4, which is (Sz_i)^2; S_i.S_i = 3/4 is three times that.
+extern "C" xd_status xd_correlations(xd_basis b, const void *psi, xd_dtype dt, const int32_t *pairs,
+                                     int npairs, int kind, double *out) {
+    using namespace xd;
+    if (!b || !psi || !out || (npairs > 0 && !pairs)) {
+        set_error("xd_correlations: NULL argument");
+        return XD_EINVAL;
+    }
+    if (b->sym) {
+        set_error("xd_correlations: U(1) blocks only (this block is symmetry-adapted)");
+        return XD_EINVAL;
+    }
+    if (dt != XD_F64 && dt != XD_F32) {
+        set_error("xd_correlations: dtype must be XD_F64 or XD_F32");
+        return XD_EINVAL;
+    }
+    if (kind != 0 && kind != 1) {
+        set_error("xd_correlations: kind must be 0 (Sz Sz) or 1 (S.S)");
+        return XD_EINVAL;
+    }
+    if (npairs < 0 || npairs > (1 << 20)) {
+        set_error("xd_correlations: npairs = %d out of range", npairs);
+        return XD_ERANGE;
+    }
+    std::vector<uint64_t> m(npairs);
+    for (int q = 0; q < npairs; ++q) {
+        const int i = pairs[2 * q], j = pairs[2 * q + 1];
+        if (i < 0 || i >= b->N || j < 0 || j >= b->N) {
+            set_error("xd_correlations: pair %d = (%d, %d) outside 0..%d", q, i, j, b->N - 1);
+            return XD_EINVAL;
+        }
+        m[q] = (1ull << i) | (1ull << j);
+    }
+    if (npairs == 0) return XD_OK;
+    if (b->dim == 0) {
+        for (int q = 0; q < npairs; ++q) out[q] = 0.0;
+        return XD_OK;
+    }
+    const U1View u = b->u1view();
+    const int grid = grid_for(u.dim, kBT, 1);
+    uint64_t *d_m = nullptr;
+    double *d_part = nullptr, *d_out = nullptr;
+    cudaError_t e = cudaMalloc((void **)&d_m, sizeof(uint64_t) * npairs);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d_part, sizeof(double) * (size_t)grid * npairs);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d_out, sizeof(double) * npairs);
+    if (e == cudaSuccess) e = cudaMemcpy(d_m, m.data(), sizeof(uint64_t) * npairs, cudaMemcpyHostToDevice);
+    xd_status s = e == cudaSuccess ? XD_OK : cuda_status(e, "xd_correlations workspace");
+    if (s == XD_OK) {
+        if (dt == XD_F64)
+            s = kind ? launch_bilinear_bp<double, false>(u, d_m, npairs, grid, psi, psi, d_part, 0)
+                     : launch_bilinear_bp<double, true>(u, d_m, npairs, grid, psi, psi, d_part, 0);
+        else
+            s = kind ? launch_bilinear_bp<float, false>(u, d_m, npairs, grid, psi, psi, d_part, 0)
+                     : launch_bilinear_bp<float, true>(u, d_m, npairs, grid, psi, psi, d_part, 0);
+    }
+    if (s == XD_OK) {
+        k_sum_columns<<<(npairs + 127) / 128, 128>>>(d_part, grid, npairs, d_out);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpy(out, d_out, sizeof(double) * npairs, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) s = cuda_status(e, "xd_correlations");
+    }
+    cudaFree(d_m);
+    cudaFree(d_part);
+    cudaFree(d_out);
+    if (s != XD_OK) return s;
+    if (kind)
+        for (int q = 0; q < npairs; ++q)
+            if (pairs[2 * q] == pairs[2 * q + 1]) out[q] *= 3.0;
     return XD_OK;
 }
 
