@@ -374,3 +374,12 @@ def lanczos_ground_state(matvec, dim, v0, steps, full_reorth=True):
         psi = psi + c[k + 1] * v
     psi = psi / np.linalg.norm(psi)
     return float(w[0]), psi
+
+
+# ----------------------------------------------------------- time evolution
+def evolve_dense(H: np.ndarray, psi0: np.ndarray, z: complex) -> np.ndarray:
+    """exp(-z H) psi0 for a dense Hermitian block H (Sec. 3.6.2: z = i t gives
+    the real-time evolution e^{-iHt}, z = tau the imaginary-time e^{-tau H}),
+    written out through the eigendecomposition H = V diag(w) V^dagger."""
+    w, V = np.linalg.eigh(H)
+    return V @ (np.exp(-z * w) * (V.conj().T @ np.asarray(psi0, dtype=np.complex128)))
