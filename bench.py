@@ -246,6 +246,24 @@ def extra_rows(hbm):
         "su2_max_dev": float(np.abs(ss - 3 * zz).max()), "sum_rule": float(ss.sum())}
     del hc, psi
     torch.cuda.empty_cache()
+    # next row 2: time evolution (Sec. 3.6.2) -- a domain wall |up..up down..down>
+    # in the open ferromagnetic Heisenberg chain, N=28 (dim 40,116,600),
+    # evolved to t = 4 by the two-pass Lanczos method
+    N28 = 28
+    hd = api.Hamiltonian(api.Basis(N28, 14, np.array([(i, i + 1) for i in range(N28 - 1)], dtype=np.int32)),
+                         [-1.0] * (N28 - 1))
+    psi0 = torch.zeros(hd.dim, dtype=torch.complex128, device="cuda")
+    psi0[hd.basis.index((1 << 14) - 1)] = 1.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    psit, info = hd.evolve(psi0, t=4.0, tol=1e-10, max_iter=300)
+    ev_s = time.perf_counter() - t0
+    out["next2_evolve_domain_wall_chain28"] = {
+        "s": ev_s, "krylov_steps": info["n_iter"], "err_estimate": info["err"],
+        "s_per_step_two_passes": ev_s / max(1, info["n_iter"]),
+        "norm_deviation": abs(float(psit.norm()) - 1.0), "dim": hd.dim}
+    del hd, psi0, psit
+    torch.cuda.empty_cache()
     # a4': symmetric 6x6 blocks
     b6, J6 = W.square_j1j2(6, 6)
     for mx in (0, 1):

@@ -189,6 +189,21 @@ xd_status xd_lanczos_ground_state(xd_ham h, int max_iter, uint64_t seed,
                                   double *beta, int *n_iter, double *evals,
                                   double *resid, void *psi0);
 
+/* Time evolution out = exp(-z H) psi0 with z = z_re + i z_im (Sec. 3.6.2:
+ * z = i t is the real-time evolution e^{-iHt}, z = tau the imaginary-time
+ * e^{-tau H}), by the memory-efficient two-pass Lanczos method the paper
+ * uses: pass 1 builds the tridiagonal T_m from psi0/|psi0| until the error
+ * estimate |psi0| beta_m |[exp(-z T_m) e_1]_m| is at most tol |psi0| (or
+ * max_iter steps), pass 2 repeats the recurrence and sums the Krylov vectors
+ * with the coefficients |psi0| exp(-z T_m) e_1.
+ * psi0, out: distinct device [dim] complex vectors (interleaved re, im
+ * doubles) on any block; 1 <= max_iter <= 1000.  Host outputs: *n_iter = m,
+ * *err = the final error estimate (absolute).  Synchronous.  Device
+ * workspace: three complex vectors. */
+xd_status xd_evolve(xd_ham h, const void *psi0, double z_re, double z_im,
+                    int max_iter, double tol, void *out, int *n_iter,
+                    double *err);
+
 /* dE0/dJ_b = <psi0| S_{i_b}.S_{j_b} |psi0> (Hellmann-Feynman with the
  * expectation values of Sec. 3.7); psi0 is a device unit vector of dtype;
  * dEdJ is [nb] host doubles.  Synchronous. */

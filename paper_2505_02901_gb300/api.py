@@ -172,6 +172,22 @@ class Hamiltonian:
         info = self._lanczos(max_iter, seed, storage, nev, psi)
         return float(info["evals"][0]), psi, info
 
+    def evolve(self, psi0: torch.Tensor, t: float = 0.0, tau: float = 0.0, max_iter: int = 200,
+               tol: float = 1e-12):
+        """exp(-(tau + i t) H) psi0 (Sec. 3.6.2 time_evolve: real time t,
+        imaginary time tau) by the two-pass Lanczos method.  psi0: complex128
+        CUDA tensor [dim].  Returns (psi, {"n_iter", "err"})."""
+        _check_vec(psi0, self.dim, "psi0")
+        if psi0.dtype != torch.complex128:
+            raise TypeError("psi0 must be complex128")
+        out = torch.empty_like(psi0)
+        n = ctypes.c_int()
+        err = ctypes.c_double()
+        torch.cuda.current_stream().synchronize()
+        check(_lib.lib().xd_evolve(self._h, _ptr(psi0), float(tau), float(t), int(max_iter), float(tol),
+                                   _ptr(out), ctypes.byref(n), ctypes.byref(err)))
+        return out, {"n_iter": n.value, "err": err.value}
+
     def energy_grad(self, psi0: torch.Tensor) -> np.ndarray:
         """dE0/dJ_b = <psi0|S_i.S_j|psi0> (Hellmann-Feynman, Sec. 3.7 inner)."""
         _check_vec(psi0, self.dim, "psi0")

@@ -123,6 +123,19 @@ __global__ void k_axpy(int64_t n, T *__restrict__ psi, T c, const T *__restrict_
         psi[i] += c * u[i];
 }
 
+// out += (cr + i ci) u on interleaved complex vectors of n entries
+__global__ void k_axpy_c(int64_t n, double2 *__restrict__ out, double cr, double ci,
+                         const double2 *__restrict__ u) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = u[i];
+        double2 o = out[i];
+        o.x += cr * v.x - ci * v.y;
+        o.y += cr * v.y + ci * v.x;
+        out[i] = o;
+    }
+}
+
 __global__ void k_sum(const double *__restrict__ part, int n, double *__restrict__ out) {
     if (threadIdx.x || blockIdx.x) return;
     double s = 0.0;
@@ -409,11 +422,224 @@ static void ritz(int n, const double *alpha, const double *beta, int nev, double
     }
 }
 
+// Eigenpairs of a symmetric n x n matrix by cyclic Jacobi rotations (the
+// Jacobi eigenvalue method): A is destroyed, Q[i*n + j] = component i of
+// eigenvector j, w[j] its eigenvalue.
+static void jacobi_eig(int n, std::vector<double> &A, std::vector<double> &Q, std::vector<double> &w) {
+    Q.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                const double a = A[(size_t)i * n + j] * A[(size_t)i * n + j];
+                tot += a;
+                if (i != j) off += a;
+            }
+        if (off <= 1e-32 * tot || off == 0.0) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                // rotation angle that zeroes A[p][q]: tan(2 phi) = 2 apq / (aqq - app)
+                const double th = (aqq - app) / (2.0 * apq);
+                const double tn = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                const double c = 1.0 / sqrt(tn * tn + 1.0), s = tn * c;
+                for (int k = 0; k < n; ++k) {  // columns p, q
+                    const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = c * akp - s * akq;
+                    A[(size_t)k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {  // rows p, q
+                    const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - s * aqk;
+                    A[(size_t)q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double qkp = Q[(size_t)k * n + p], qkq = Q[(size_t)k * n + q];
+                    Q[(size_t)k * n + p] = c * qkp - s * qkq;
+                    Q[(size_t)k * n + q] = s * qkp + c * qkq;
+                }
+            }
+    }
+    w.resize(n);
+    for (int i = 0; i < n; ++i) w[i] = A[(size_t)i * n + i];
+}
+
+// c = exp(-z T) e_1 for the tridiagonal T = tridiag(beta, alpha, beta) of
+// size m: T = Q diag(w) Q^T, c_k = sum_j Q[k][j] exp(-z w_j) Q[0][j].
+static void expm_tridiag_e1(int m, const double *alpha, const double *beta, double zr, double zi,
+                            std::vector<double> &cre, std::vector<double> &cim) {
+    std::vector<double> A((size_t)m * m, 0.0), Q, w;
+    for (int k = 0; k < m; ++k) {
+        A[(size_t)k * m + k] = alpha[k];
+        if (k + 1 < m) A[(size_t)k * m + k + 1] = A[(size_t)(k + 1) * m + k] = beta[k];
+    }
+    jacobi_eig(m, A, Q, w);
+    // shift by the smallest eigenvalue against overflow of exp(-tau w)
+    double wmin = w.empty() ? 0.0 : *std::min_element(w.begin(), w.end());
+    if (zr <= 0.0) wmin = 0.0;
+    cre.assign(m, 0.0);
+    cim.assign(m, 0.0);
+    for (int j = 0; j < m; ++j) {
+        const double mag = exp(-zr * (w[j] - wmin)), ph = -zi * w[j];
+        const double er = mag * cos(ph), ei = mag * sin(ph);
+        const double q0 = Q[j];  // Q[0][j]
+        for (int k = 0; k < m; ++k) {
+            cre[k] += Q[(size_t)k * m + j] * q0 * er;
+            cim[k] += Q[(size_t)k * m + j] * q0 * ei;
+        }
+    }
+    if (zr > 0.0) {  // undo the shift: exp(-zr wmin) overall
+        const double f = exp(-zr * wmin);
+        for (int k = 0; k < m; ++k) {
+            cre[k] *= f;
+            cim[k] *= f;
+        }
+    }
+}
+
+// H on an interleaved complex vector: U(1) blocks (H real) as two real
+// right-hand sides, symmetry-adapted blocks through the complex kernel.
+static xd_status apply_c(xd_ham_s *h, const double *x, double *y, cudaStream_t st) {
+    if (!h->b->sym) return u1_apply(h, x, y, XD_F64, 2, st);
+    return sym_apply(h, x, y, XD_C128, st);
+}
+
+// exp(-z H) psi0 by the two-pass Lanczos method (Sec. 3.6.2): pass 1 builds
+// the tridiagonal T_m from v_1 = psi0 / |psi0| until the error estimate
+// |psi0| beta_m |[exp(-z T_m) e_1]_m| drops below tol |psi0|; pass 2 reruns
+// the same recurrence (recorded alpha, beta) and sums |psi0| c_k v_k.
+static xd_status evolve_run(xd_ham_s *h, const double *psi0, double zr, double zi, int max_iter,
+                            double tol, double *out, int *n_iter, double *err) {
+    const xd_basis_s *b = h->b;
+    const int64_t nc = b->dim, n = 2 * nc;
+    cudaStream_t st = 0;
+    LzWork lw;
+    lw.grid = grid_for(n, kThreads, 8);
+    XD_TRY(ensure_lanczos_partials(h, lw.grid));
+    lw.part = h->d_lzpart;
+    lw.scal = h->d_scal;
+    const size_t vbytes = (size_t)n * sizeof(double);
+    double *buf[3] = {nullptr, nullptr, nullptr};
+    for (int k = 0; k < 3; ++k) {
+        cudaError_t e = cudaMalloc((void **)&buf[k], std::max<size_t>(vbytes, 16));
+        if (e != cudaSuccess) {
+            for (int q = 0; q < k; ++q) cudaFree(buf[q]);
+            return cuda_status(e, "cudaMalloc(evolution vectors)");
+        }
+    }
+    std::vector<double> alpha(max_iter), beta(max_iter), cre, cim;
+    xd_status rc = XD_OK;
+    double nrm0 = 0.0, est = INFINITY;
+    int m = 0;
+    for (int pass = 0; pass < 2 && rc == XD_OK; ++pass) {
+        double *up = buf[0], *u = buf[1], *w = buf[2];
+        if (pass == 1) {
+            cudaError_t e = cudaMemsetAsync(out, 0, vbytes, st);
+            if (e != cudaSuccess) {
+                rc = cuda_status(e, "cudaMemsetAsync");
+                break;
+            }
+        }
+        cudaError_t e = cudaMemcpyAsync(u, psi0, vbytes, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(up, 0, vbytes, st);
+        if (e != cudaSuccess) {
+            rc = cuda_status(e, "evolution start");
+            break;
+        }
+        if (pass == 0) {
+            double nrm2 = 0.0;
+            if ((rc = lz_axpby<double>(n, u, 1.0, nullptr, 0.0, u, lw, st, &nrm2)) != XD_OK) break;
+            nrm0 = sqrt(nrm2);
+            if (!(nrm0 > 0.0)) {  // exp(-zH) 0 = 0
+                m = 0;
+                est = 0.0;
+                cudaMemsetAsync(out, 0, vbytes, st);
+                break;
+            }
+        }
+        double sig = 1.0 / nrm0, sig_prev = 0.0, beta_prev = 0.0, amax = 0.0;
+        const int steps = pass == 0 ? max_iter : m;
+        for (int k = 0; k < steps; ++k) {
+            if (pass == 1) {
+                // out += |psi0| c_k v_k, v_k = sig u
+                k_axpy_c<<<lw.grid, kThreads, 0, st>>>(nc, (double2 *)out, nrm0 * cre[k] * sig,
+                                                       nrm0 * cim[k] * sig, (const double2 *)u);
+                cudaError_t e2 = cudaGetLastError();
+                if (e2 != cudaSuccess) {
+                    rc = cuda_status(e2, "k_axpy_c");
+                    break;
+                }
+                if (k == steps - 1) break;
+                if ((rc = apply_c(h, u, w, st)) != XD_OK) break;
+                if ((rc = lz_axpby<double>(n, w, sig, up, -beta_prev * sig_prev, nullptr, lw, st, nullptr)) != XD_OK) break;
+                if ((rc = lz_axpby<double>(n, w, 1.0, u, -alpha[k] * sig, nullptr, lw, st, nullptr)) != XD_OK) break;
+                beta_prev = beta[k];
+            } else {
+                if ((rc = apply_c(h, u, w, st)) != XD_OK) break;
+                double d1 = 0.0, d2 = 0.0;
+                if ((rc = lz_axpby<double>(n, w, sig, up, -beta_prev * sig_prev, u, lw, st, &d1)) != XD_OK) break;
+                const double a = sig * d1;
+                if ((rc = lz_axpby<double>(n, w, 1.0, u, -a * sig, w, lw, st, &d2)) != XD_OK) break;
+                const double bt = sqrt(std::max(d2, 0.0));
+                alpha[k] = a;
+                beta[k] = bt;
+                amax = std::max(amax, fabs(a));
+                beta_prev = bt;
+                m = k + 1;
+                const bool exact = bt < 1e-13 * amax;
+                if (exact || k == steps - 1 || (k + 1) % 4 == 0) {
+                    expm_tridiag_e1(m, alpha.data(), beta.data(), zr, zi, cre, cim);
+                    est = exact ? 0.0 : nrm0 * bt * hypot(cre[m - 1], cim[m - 1]);
+                    if (est <= tol * nrm0 || exact) break;
+                }
+            }
+            sig_prev = sig;
+            sig = 1.0 / beta_prev;
+            double *tmp = up;
+            up = u;
+            u = w;
+            w = tmp;
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    for (int q = 0; q < 3; ++q) cudaFree(buf[q]);
+    if (rc == XD_OK && e != cudaSuccess) rc = cuda_status(e, "time evolution");
+    if (rc == XD_OK) {
+        *n_iter = m;
+        *err = est;
+    }
+    return rc;
+}
+
 }  // namespace xd
 
 using namespace xd;
 
 extern "C" {
+
+xd_status xd_evolve(xd_ham h, const void *psi0, double z_re, double z_im, int max_iter, double tol,
+                    void *out, int *n_iter, double *err) {
+    if (!h || !psi0 || !out || !n_iter || !err) {
+        set_error("xd_evolve: NULL argument");
+        return XD_EINVAL;
+    }
+    if (psi0 == out) {
+        set_error("xd_evolve: psi0 and out must be distinct");
+        return XD_EINVAL;
+    }
+    if (max_iter < 1 || max_iter > 1000) {
+        set_error("xd_evolve: max_iter = %d outside 1..1000", max_iter);
+        return XD_EINVAL;
+    }
+    if (!std::isfinite(z_re) || !std::isfinite(z_im) || !(tol >= 0.0)) {
+        set_error("xd_evolve: z and tol must be finite, tol >= 0");
+        return XD_EINVAL;
+    }
+    return evolve_run(h, (const double *)psi0, z_re, z_im, max_iter, tol, (double *)out, n_iter, err);
+}
 
 xd_status xd_lanczos_eigenvalues(xd_ham h, int max_iter, uint64_t seed, xd_dtype dt, int nev,
                                  double *alpha, double *beta, int *n_iter, double *evals,
