@@ -383,3 +383,46 @@ def evolve_dense(H: np.ndarray, psi0: np.ndarray, z: complex) -> np.ndarray:
     written out through the eigendecomposition H = V diag(w) V^dagger."""
     w, V = np.linalg.eigh(H)
     return V @ (np.exp(-z * w) * (V.conj().T @ np.asarray(psi0, dtype=np.complex128)))
+
+
+# ------------------------------------------------------------ thermodynamics
+def ftlm_tridiagonals(matvec, starts, steps: int):
+    """Finite-temperature Lanczos (the thermal pure quantum state / FTLM
+    ensemble of the paper's thermodynamics examples): one plain Lanczos run
+    (no reorthogonalisation) per start vector r, returning the lists of
+    (alpha, beta) and the norms |r|."""
+    out = []
+    for r in starts:
+        a, b = lanczos(matvec, r.size, r, steps, full_reorth=False, tol=0.0)
+        out.append((a, b, float(np.linalg.norm(r))))
+    return out
+
+
+def ftlm_thermo(tri, dim: int, temps, exact_trace: bool = False):
+    """Z, E and C at the temperatures T from the tridiagonals T_r:
+    T_r = Q diag(eps) Q^T, weights |Q_0j|^2, and with R starts
+        Z = (dim / R) sum_r sum_j |Q_0j|^2 e^{-eps_j / T}
+        E = (dim / R) sum ... eps_j e^{-eps_j/T} / Z,  C = (<E^2> - E^2) / T^2.
+    Random starts are normalised to unit length; with exact_trace the starts
+    are taken as given (an orthonormal basis gives the trace exactly, so the
+    prefactor dim / R is then 1)."""
+    R = len(tri)
+    pref = 1.0 if exact_trace else dim / R
+    res = []
+    for T in temps:
+        z = e1 = e2 = 0.0
+        shift = min(np.linalg.eigvalsh(_tri(a, b)).min() for a, b, _ in tri)
+        for a, b, nr in tri:
+            w, Q = np.linalg.eigh(_tri(a, b))
+            wt = Q[0, :] ** 2 * np.exp(-(w - shift) / T)
+            z += wt.sum()
+            e1 += (w * wt).sum()
+            e2 += (w * w * wt).sum()
+        E = e1 / z
+        res.append((pref * z * np.exp(-shift / T), E, (e2 / z - E * E) / T ** 2))
+    return res
+
+
+def _tri(a, b):
+    n = len(a)
+    return np.diag(a) + np.diag(b[: n - 1], 1) + np.diag(b[: n - 1], -1)
