@@ -264,6 +264,22 @@ def extra_rows(hbm):
         "norm_deviation": abs(float(psit.norm()) - 1.0), "dim": hd.dim}
     del hd, psi0, psit
     torch.cuda.empty_cache()
+    # next row 3: thermodynamics by finite-temperature Lanczos (R random
+    # starts through the eight-vector product) on the 4x6 J1-J2 square lattice
+    b46, J46 = W.square_j1j2(4, 6)
+    hf = api.Hamiltonian(api.Basis(24, 12, b46), J46)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fa, fb, fn = hf.ftlm(32, 80, SEED)
+    ftlm_s = time.perf_counter() - t0
+    temps = [0.1, 0.3, 1.0, 3.0]
+    Zt, Et, Ct = api.ftlm_thermo(fa, fb, fn, hf.dim, temps)
+    out["next3_ftlm_square4x6"] = {
+        "s": ftlm_s, "starts": 32, "steps": 80, "dim": hf.dim,
+        "s_per_step_of_8_vectors": ftlm_s / (4 * 80),
+        "T": temps, "E_per_site": [float(e) / 24 for e in Et], "C_per_site": [float(c) / 24 for c in Ct]}
+    del hf
+    torch.cuda.empty_cache()
     # a4': symmetric 6x6 blocks
     b6, J6 = W.square_j1j2(6, 6)
     for mx in (0, 1):

@@ -204,6 +204,25 @@ xd_status xd_evolve(xd_ham h, const void *psi0, double z_re, double z_im,
                     int max_iter, double tol, void *out, int *n_iter,
                     double *err);
 
+/* Finite-temperature Lanczos / thermal pure quantum states (the
+ * thermodynamics examples of Sec. 4, Sugiura-Shimizu TPQ and the FTLM of
+ * Jaklic-Prelovsek): R seeded random start vectors (start r is the
+ * standard-normal vector of xd_random_vector with seed + r), each run
+ * through M plain Lanczos steps (a run whose beta drops below 1e-13
+ * max|alpha| stops early), eight at a time through the eight-vector product.
+ * U(1) blocks.  Host outputs: alpha, beta [R][M] (zero past n_iter[r]),
+ * n_iter [R].  Synchronous.  Device workspace: three [dim][8] FP64 arrays. */
+xd_status xd_ftlm(xd_ham h, int R, int M, uint64_t seed, double *alpha,
+                  double *beta, int *n_iter);
+
+/* Thermodynamics from the tridiagonals of xd_ftlm (host only): with T_r =
+ * Q diag(eps) Q^T and weights |Q_0j|^2, at each temperature T[q] > 0
+ *   Z = (dim / R) sum_{r,j} |Q_0j|^2 e^{-eps_j/T},  E = <eps>,  C = (<eps^2> - E^2) / T^2.
+ * Outputs Z, E, C: host [nT]. */
+xd_status xd_ftlm_thermo(int R, int M, const double *alpha, const double *beta,
+                         const int *n_iter, double dim, int nT,
+                         const double *temps, double *Z, double *E, double *C);
+
 /* dE0/dJ_b = <psi0| S_{i_b}.S_{j_b} |psi0> (Hellmann-Feynman with the
  * expectation values of Sec. 3.7); psi0 is a device unit vector of dtype;
  * dEdJ is [nb] host doubles.  Synchronous. */

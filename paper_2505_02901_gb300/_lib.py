@@ -47,6 +47,8 @@ SIGNATURES = {
     "xd_apply_bilinear_noalloc": (_i, [_vp, _vp, _vp, _i, _vp, _vp]),
     "xd_correlations": (_i, [_vp, _vp, _i, _c.POINTER(_c.c_int32), _i, _i, _dp]),
     "xd_evolve": (_i, [_vp, _vp, _c.c_double, _c.c_double, _i, _c.c_double, _vp, _c.POINTER(_i), _dp]),
+    "xd_ftlm": (_i, [_vp, _i, _i, _u64, _dp, _dp, _c.POINTER(_i)]),
+    "xd_ftlm_thermo": (_i, [_i, _i, _dp, _dp, _c.POINTER(_i), _c.c_double, _i, _dp, _dp, _dp, _dp]),
     "xd_lanczos_eigenvalues": (_i, [_vp, _i, _u64, _i, _i, _dp, _dp, _c.POINTER(_i), _dp, _dp]),
     "xd_lanczos_ground_state": (_i, [_vp, _i, _u64, _i, _i, _dp, _dp, _c.POINTER(_i), _dp, _dp, _vp]),
     "xd_energy_grad": (_i, [_vp, _vp, _i, _dp]),

@@ -188,6 +188,18 @@ class Hamiltonian:
                                    _ptr(out), ctypes.byref(n), ctypes.byref(err)))
         return out, {"n_iter": n.value, "err": err.value}
 
+    def ftlm(self, R: int = 16, M: int = 80, seed: int = 1):
+        """Finite-temperature Lanczos tridiagonals of R random starts (seed + r),
+        M steps each; returns (alpha [R, M], beta [R, M], n_iter [R])."""
+        a = np.zeros((R, M))
+        b = np.zeros((R, M))
+        n = np.zeros(R, dtype=np.int32)
+        torch.cuda.current_stream().synchronize()
+        dp = ctypes.POINTER(ctypes.c_double)
+        check(_lib.lib().xd_ftlm(self._h, int(R), int(M), ctypes.c_uint64(seed), a.ctypes.data_as(dp),
+                                 b.ctypes.data_as(dp), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return a, b, n
+
     def energy_grad(self, psi0: torch.Tensor) -> np.ndarray:
         """dE0/dJ_b = <psi0|S_i.S_j|psi0> (Hellmann-Feynman, Sec. 3.7 inner)."""
         _check_vec(psi0, self.dim, "psi0")
@@ -202,6 +214,21 @@ class Hamiltonian:
         if h is not None and h.value and _lib._lib is not None:
             _lib._lib.xd_ham_destroy(h)
             self._h = None
+
+
+def ftlm_thermo(alpha: np.ndarray, beta: np.ndarray, n_iter: np.ndarray, dim: int, temps):
+    """(Z, E, C) at the temperatures from the tridiagonals of Hamiltonian.ftlm."""
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    n_iter = np.ascontiguousarray(n_iter, dtype=np.int32)
+    T = np.ascontiguousarray(np.asarray(temps, dtype=np.float64).reshape(-1))
+    Z, E, C = np.zeros(T.size), np.zeros(T.size), np.zeros(T.size)
+    dp = ctypes.POINTER(ctypes.c_double)
+    check(_lib.lib().xd_ftlm_thermo(alpha.shape[0], alpha.shape[1], alpha.ctypes.data_as(dp), beta.ctypes.data_as(dp),
+                                    n_iter.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), float(dim), T.size,
+                                    T.ctypes.data_as(dp), Z.ctypes.data_as(dp), E.ctypes.data_as(dp),
+                                    C.ctypes.data_as(dp)))
+    return Z, E, C
 
 
 def random_vector(dim: int, seed: int, dtype=torch.float64, out=None) -> torch.Tensor:
@@ -283,4 +310,4 @@ def ground_energy(ham: Hamiltonian, J: torch.Tensor, max_iter=200, seed=1, stora
 
 
 __all__ = ["Basis", "Hamiltonian", "random_vector", "batch_apply", "heisenberg_apply",
-           "ground_energy", "HeisenbergApply", "GroundEnergy", "XDError"]
+           "ground_energy", "HeisenbergApply", "GroundEnergy", "XDError", "ftlm_thermo"]

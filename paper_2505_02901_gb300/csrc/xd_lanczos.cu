@@ -123,6 +123,54 @@ __global__ void k_axpy(int64_t n, T *__restrict__ psi, T c, const T *__restrict_
         psi[i] += c * u[i];
 }
 
+// Eight independent vectors stored row-major [rows][8] (column c is vector
+// c): w_c = a_c w_c + b_c z_c, then part = <w_c, v_c> (mode 1) or <w_c, w_c>
+// (mode 2) per column, in FP64, fixed order (per-CTA partials [grid][8]).
+struct Coef8 {
+    double a[8], b[8];
+};
+
+__global__ void __launch_bounds__(kThreads) k_axpby_dot8(int64_t rows, double *__restrict__ w, Coef8 co,
+                                                         const double *__restrict__ z,
+                                                         const double *__restrict__ v, int mode,
+                                                         double *__restrict__ part) {
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
+         i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            double t = co.a[c] * w[i * 8 + c];
+            if (z) t = fma(co.b[c], z[i * 8 + c], t);
+            w[i * 8 + c] = t;
+            if (mode == 1) acc[c] = fma(t, v[i * 8 + c], acc[c]);
+            else if (mode == 2) acc[c] = fma(t, t, acc[c]);
+        }
+    }
+    if (!mode) return;
+    __shared__ double red[kThreads / 32][8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        double s = acc[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][c] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        double s = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q][threadIdx.x];
+        part[(size_t)blockIdx.x * 8 + threadIdx.x] = s;
+    }
+}
+
+// out[c] = sum over CTAs of part[cta][c], fixed order
+__global__ void k_sum8(const double *__restrict__ part, int n, double *__restrict__ out) {
+    if (threadIdx.x >= 8 || blockIdx.x) return;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[(size_t)i * 8 + threadIdx.x];
+    out[threadIdx.x] = s;
+}
+
 // out += (cr + i ci) u on interleaved complex vectors of n entries
 __global__ void k_axpy_c(int64_t n, double2 *__restrict__ out, double cr, double ci,
                          const double2 *__restrict__ u) {
@@ -614,11 +662,173 @@ static xd_status evolve_run(xd_ham_s *h, const double *psi0, double zr, double z
     return rc;
 }
 
+// w_c = a_c w_c + b_c z_c on eight columns; with want != 0 the per-column
+// dots (mode 1 with v, mode 2 with itself) land in host dots[8].
+static xd_status axpby8(int64_t rows, double *w, const Coef8 &co, const double *z, const double *v, int mode,
+                        const LzWork &lw, cudaStream_t st, double *dots) {
+    k_axpby_dot8<<<lw.grid, kThreads, 0, st>>>(rows, w, co, z, v, mode, lw.part);
+    XD_CUDA(cudaGetLastError());
+    if (mode) {
+        k_sum8<<<1, 32, 0, st>>>(lw.part, lw.grid, lw.scal);
+        XD_CUDA(cudaGetLastError());
+        XD_CUDA(cudaMemcpyAsync(dots, lw.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        XD_CUDA(cudaStreamSynchronize(st));
+    }
+    return XD_OK;
+}
+
+// Finite-temperature Lanczos: R seeded random starts (start r is the
+// standard-normal vector of seed + r), eight at a time through the 8-wide
+// product, M plain Lanczos steps each (a column whose beta falls below
+// 1e-13 max|alpha| stops there).  alpha, beta: host [R][M]; n_iter: [R].
+static xd_status ftlm_run(xd_ham_s *h, int R, int M, uint64_t seed, double *alpha, double *beta, int *n_iter) {
+    const xd_basis_s *b = h->b;
+    const int64_t rows = b->dim, n = rows * 8;
+    cudaStream_t st = 0;
+    LzWork lw;
+    lw.grid = grid_for(rows, kThreads, 8);
+    XD_TRY(ensure_lanczos_partials(h, lw.grid * 8));
+    lw.part = h->d_lzpart;
+    lw.scal = h->d_scal;
+    const size_t vbytes = (size_t)n * sizeof(double);
+    double *buf[3] = {nullptr, nullptr, nullptr};
+    for (int k = 0; k < 3; ++k) {
+        cudaError_t e = cudaMalloc((void **)&buf[k], std::max<size_t>(vbytes, 16));
+        if (e != cudaSuccess) {
+            for (int q = 0; q < k; ++q) cudaFree(buf[q]);
+            return cuda_status(e, "cudaMalloc(FTLM vectors)");
+        }
+    }
+    xd_status rc = XD_OK;
+    for (int r0 = 0; r0 < R && rc == XD_OK; r0 += 8) {
+        double *up = buf[0], *u = buf[1], *w = buf[2];
+        for (int c = 0; c < 8; ++c) {
+            k_random<double><<<lw.grid, kThreads, 0, st>>>(rows, seed + (uint64_t)(r0 + c), u + c, 8);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemsetAsync(up, 0, vbytes, st);
+        if (e != cudaSuccess) {
+            rc = cuda_status(e, "FTLM start");
+            break;
+        }
+        Coef8 one{};
+        for (int c = 0; c < 8; ++c) one.a[c] = 1.0;
+        double d[8], sig[8], sigp[8], bp[8], amax[8];
+        bool live[8];
+        if ((rc = axpby8(rows, u, one, nullptr, nullptr, 2, lw, st, d)) != XD_OK) break;
+        for (int c = 0; c < 8; ++c) {
+            sig[c] = d[c] > 0.0 ? 1.0 / sqrt(d[c]) : 0.0;
+            sigp[c] = bp[c] = amax[c] = 0.0;
+            live[c] = d[c] > 0.0;
+            if (r0 + c < R) n_iter[r0 + c] = 0;
+        }
+        for (int k = 0; k < M && rc == XD_OK; ++k) {
+            if ((rc = u1_apply(h, u, w, XD_F64, 8, st)) != XD_OK) break;
+            Coef8 c1{}, c2{};
+            for (int c = 0; c < 8; ++c) {
+                c1.a[c] = sig[c];
+                c1.b[c] = -bp[c] * sigp[c];
+            }
+            if ((rc = axpby8(rows, w, c1, up, u, 1, lw, st, d)) != XD_OK) break;
+            double a[8];
+            for (int c = 0; c < 8; ++c) {
+                a[c] = sig[c] * d[c];
+                c2.a[c] = 1.0;
+                c2.b[c] = -a[c] * sig[c];
+            }
+            if ((rc = axpby8(rows, w, c2, u, nullptr, 2, lw, st, d)) != XD_OK) break;
+            for (int c = 0; c < 8; ++c) {
+                const double bt = sqrt(std::max(d[c], 0.0));
+                if (live[c] && r0 + c < R) {
+                    alpha[(size_t)(r0 + c) * M + k] = a[c];
+                    beta[(size_t)(r0 + c) * M + k] = bt;
+                    n_iter[r0 + c] = k + 1;
+                    amax[c] = std::max(amax[c], fabs(a[c]));
+                    if (bt < 1e-13 * amax[c]) live[c] = false;
+                }
+                sigp[c] = sig[c];
+                bp[c] = bt;
+                sig[c] = live[c] && bt > 0.0 ? 1.0 / bt : 0.0;
+                if (!live[c]) bp[c] = 0.0;
+            }
+            double *tmp = up;
+            up = u;
+            u = w;
+            w = tmp;
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    for (int q = 0; q < 3; ++q) cudaFree(buf[q]);
+    if (rc == XD_OK && e != cudaSuccess) rc = cuda_status(e, "FTLM");
+    return rc;
+}
+
 }  // namespace xd
 
 using namespace xd;
 
 extern "C" {
+
+xd_status xd_ftlm(xd_ham h, int R, int M, uint64_t seed, double *alpha, double *beta, int *n_iter) {
+    if (!h || !alpha || !beta || !n_iter) {
+        set_error("xd_ftlm: NULL argument");
+        return XD_EINVAL;
+    }
+    if (h->b->sym) {
+        set_error("xd_ftlm: U(1) blocks only (the eight-vector product)");
+        return XD_EINVAL;
+    }
+    if (R < 1 || R > (1 << 16) || M < 1 || M > 2000) {
+        set_error("xd_ftlm: R = %d or M = %d out of range", R, M);
+        return XD_EINVAL;
+    }
+    for (size_t q = 0; q < (size_t)R * M; ++q) alpha[q] = beta[q] = 0.0;
+    return ftlm_run(h, R, M, seed, alpha, beta, n_iter);
+}
+
+xd_status xd_ftlm_thermo(int R, int M, const double *alpha, const double *beta, const int *n_iter, double dim,
+                         int nT, const double *temps, double *Z, double *E, double *C) {
+    if (!alpha || !beta || !n_iter || !temps || !Z || !E || !C || R < 1 || M < 1 || nT < 0) {
+        set_error("xd_ftlm_thermo: bad argument");
+        return XD_EINVAL;
+    }
+    // eigenpairs of every tridiagonal; weights |Q_0j|^2
+    std::vector<std::vector<double>> ev(R), wt(R);
+    double shift = INFINITY;
+    for (int r = 0; r < R; ++r) {
+        const int m = std::min(std::max(n_iter[r], 0), M);
+        std::vector<double> A((size_t)m * m, 0.0), Q;
+        for (int k = 0; k < m; ++k) {
+            A[(size_t)k * m + k] = alpha[(size_t)r * M + k];
+            if (k + 1 < m) A[(size_t)k * m + k + 1] = A[(size_t)(k + 1) * m + k] = beta[(size_t)r * M + k];
+        }
+        jacobi_eig(m, A, Q, ev[r]);
+        wt[r].resize(m);
+        for (int j = 0; j < m; ++j) {
+            wt[r][j] = Q[j] * Q[j];
+            shift = std::min(shift, ev[r][j]);
+        }
+    }
+    for (int q = 0; q < nT; ++q) {
+        const double T = temps[q];
+        if (!(T > 0.0)) {
+            set_error("xd_ftlm_thermo: temperature %d is not positive", q);
+            return XD_EINVAL;
+        }
+        double z = 0.0, e1 = 0.0, e2 = 0.0;
+        for (int r = 0; r < R; ++r)
+            for (size_t j = 0; j < ev[r].size(); ++j) {
+                const double p = wt[r][j] * exp(-(ev[r][j] - shift) / T);
+                z += p;
+                e1 += ev[r][j] * p;
+                e2 += ev[r][j] * ev[r][j] * p;
+            }
+        E[q] = e1 / z;
+        C[q] = (e2 / z - E[q] * E[q]) / (T * T);
+        Z[q] = dim / R * z * exp(-shift / T);
+    }
+    return XD_OK;
+}
 
 xd_status xd_evolve(xd_ham h, const void *psi0, double z_re, double z_im, int max_iter, double tol,
                     void *out, int *n_iter, double *err) {
