@@ -38,7 +38,7 @@ FORM_NOTE = {
 # dram__bytes_read.sum + dram__bytes_write.sum of one apply launch at this
 # workload (ncu, profiles/apply_4x8_*.md); None until measured for the
 # kernel as it stands
-TRAFFIC = {"f32": 70.92e9, "f64": 146.00e9}
+TRAFFIC = {"f32": 71.64e9, "f64": 146.00e9}
 # the kernel each form's product runs at this workload
 KERNEL = {"f32": "k_spmm<12>", "f64": "k_block_apply<double, 16, 1>"}
 
