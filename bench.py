@@ -159,6 +159,21 @@ def _event_time(fn, reps=3):
     return e0.elapsed_time(e1) / reps
 
 
+def max_over_ranks(ms: float, dist=None, device: str = "cuda") -> float:
+    """The slowest rank's time (every rank runs the same replica workload)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, ms: float) -> float:
+    """Units all ranks processed per second over the slowest rank's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def _lanczos_steady(ham, dtype, iters, short=2):
     """Seconds per Lanczos iteration in steady state: the wall time of a run
     of short + iters steps minus that of a run of `short` steps (both pay the
@@ -442,11 +457,7 @@ def main():
                 ev[2 * k + 1].record(stream)
             t1.record(stream)
             barrier()
-        total = t0.elapsed_time(t1)
-        if dist is not None:
-            t = torch.tensor([total], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
+        total = max_over_ranks(t0.elapsed_time(t1), dist)
         kern = statistics.mean(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(steps))
         del x, y
         torch.cuda.empty_cache()
@@ -466,7 +477,7 @@ def main():
         compulsory = 2 * esize * dim
         achieved = compulsory / (kern_ms / 1e3) / 1e9
         forms[form] = {
-            "value": world * elements / (ms_step / 1e3), "unit": "elements/s", "ms_per_step": ms_step,
+            "value": whole_job_rate(world, elements, ms_step), "unit": "elements/s", "ms_per_step": ms_step,
             "steps": steps, "kernel_ms": kern_ms, "hbm_gbs_compulsory": achieved,
             "roofline_frac": achieved / hbm,
             "lanczos_s_per_iter": lanczos_s_per_iter(form, args.lanczos_steps),
@@ -492,7 +503,7 @@ def main():
         yh.copy_(y, non_blocking=True)
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dist)
     del xh, yh, xd, y
 
     line = {
@@ -512,7 +523,7 @@ def main():
                      "note": f"achieved = compulsory 2*{esize}*dim bytes per H.v / mean launch time"},
         "forms": forms,
         "clocks": clk.summary(),
-        "e2e": {"value": world * elements / (e2e_ms / 1e3), "unit": "elements/s",
+        "e2e": {"value": whole_job_rate(world, elements, e2e_ms), "unit": "elements/s",
                 "h2d_bytes_per_step": esize * dim, "d2h_bytes_per_step": esize * dim},
         "gpu_launches": fh["steps"],
     }
