@@ -192,6 +192,9 @@ xd_status spmm_layout_build(xd_basis_s *b);
 void spmm_layout_free(xd_basis_s *b);
 xd_status spmm_ham_tables(xd_ham_s *h);
 xd_status spmm_apply(const xd_ham_s *h, const void *x, void *y, cudaStream_t st);
+// eight right-hand sides on the same layout (xd_u1_spmm8.cu); x, y [dim][8] FP32
+bool spmm8_usable(const xd_ham_s *h, const void *x, const void *y);
+xd_status spmm8_apply(const xd_ham_s *h, const void *x, void *y, cudaStream_t st);
 // forget cached batch plans that use this handle (xd_batch.cu)
 void batch_forget(const xd_ham_s *h);
 // workspace helper

@@ -242,6 +242,7 @@ static xd_status launch_apply(const xd_ham_s *h, const void *x, void *y, cudaStr
 xd_status u1_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, int nvec,
                    cudaStream_t st) {
     if (nvec == 1 && dt == XD_F32 && h->b->spmm.ok) return spmm_apply(h, x, y, st);
+    if (nvec == 8 && dt == XD_F32 && spmm8_usable(h, x, y)) return spmm8_apply(h, x, y, st);
     if (nvec == 1 && h->b->blk.ok) return block_apply(h, x, y, dt, st);
     if (dt == XD_F64) {
         switch (nvec) {

@@ -172,3 +172,24 @@ def test_square4x8_full_size(orc, dtype, tol):
     assert rel_l2(ys, yo) <= tol
     del x, y
     torch.cuda.empty_cache()
+
+
+def test_eight_rhs_large_block(orc):
+    """Eight FP32 right-hand sides on a ragged N=26 block with prefix, postfix
+    and cross bonds (the eight-vector form of the batched layout), and the
+    same product from a vector that is not 16-byte aligned (generic kernel)."""
+    A = api()
+    N, nup = 26, 12
+    bonds, J = W.random_bonds(N, 52, 26), W.uniform_couplings(52, 26, -1.0, 1.0)
+    st = orc.enumerate_states(N, nup)
+    ham = A.Hamiltonian(A.Basis(N, nup, bonds), J)
+    X = np.stack([orc.rng_normal(30 + k, 0, st.size) for k in range(8)], axis=1).astype(np.float32)
+    Yo = orc.apply_u1(N, st, bonds, J, X.astype(np.float64))
+    x = torch.from_numpy(X).cuda().contiguous()
+    y = ham.apply(x).cpu().numpy()
+    assert rel_l2(y, Yo) <= 2e-6
+    buf = torch.empty(st.size * 8 + 1, dtype=torch.float32, device="cuda")
+    xu = buf[1:].view(st.size, 8)
+    xu.copy_(x)
+    yu = ham.apply(xu).cpu().numpy()
+    assert rel_l2(yu, Yo) <= 2e-6
