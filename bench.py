@@ -399,6 +399,22 @@ def run_reference(args):
     return 0
 
 
+def run_sym_chain(n: int):
+    """The symmetric product on the n-site chain block with D_n, four times."""
+    import torch
+
+    from paper_2505_02901_gb300 import api, build, workloads as W
+    build.build()
+    basis = api.Basis(n, n // 2, W.chain(n),
+                      symmetry=(W.chain_dihedral(n), W.chain_dihedral_characters(n, 0, 1)))
+    h = api.Hamiltonian(basis, [1.0] * n)
+    x = api.random_vector(basis.dim, SEED, torch.float64)
+    y = torch.empty_like(x)
+    ms = _event_time(lambda: h.apply(x, out=y), reps=3)
+    print(json.dumps({"case": "sym-chain", "N": n, "group": 2 * n, "dim": basis.dim, "ms": ms}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -410,6 +426,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only", action="store_true", help="time the headline form only")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-row measurements")
+    ap.add_argument("--case", default="bench", choices=["bench", "sym-chain"],
+                    help="sym-chain: only the symmetric product of the N-site chain with its "
+                         "translations and reflections (fully symmetric irrep), four times, for "
+                         "profiling captures (N from --chain-n)")
+    ap.add_argument("--chain-n", type=int, default=32)
     ap.add_argument("--lattice", default="4x8",
                     help="LxxLy of the periodic J1-J2 lattice (4x8 is the benchmark; smaller "
                          "ones serve ncu captures, e.g. 4x7)")
@@ -422,6 +443,8 @@ def main():
                     f"dim {math.comb(N, NUP)}, y = H x")
     if args.impl == "reference":
         return run_reference(args)
+    if args.case == "sym-chain":
+        return run_sym_chain(args.chain_n)
 
     import numpy as np
     import torch
