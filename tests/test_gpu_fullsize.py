@@ -104,3 +104,48 @@ def test_c3_ladder28_gradient(orc):
         em = ham.lanczos(max_iter=200, seed=3)["evals"][0]
         assert abs((ep - em) / (2 * h) - g[b]) < 1e-5
     ham.set_couplings(J)
+
+
+def test_paper_chain36_u1_and_dihedral_sector(orc):
+    """The paper's N=36 chain benchmarks: the U(1) block (dim 9,075,135,300,
+    FP32 prefix-block product at P = 24) on sampled rows against the oracle;
+    the D_36 fully symmetric block (dim 126,068,558 by Burnside, ring path of
+    the orbit search) with valid ascending representatives and Hermiticity;
+    and the lowest energy of that block equal to the U(1) ground energy (the
+    chain's ground state at N = 36 is translation and reflection invariant)."""
+    A = api()
+    N = 36
+    bonds, J = W.chain(N), np.ones(N)
+    ham = A.Hamiltonian(A.Basis(N, N // 2, bonds), J)
+    seed = 11
+    x = A.random_vector(ham.dim, seed, torch.float32)
+    y = ham.apply(x)
+    del x
+    rows = np.concatenate([[0, ham.dim - 1], np.random.default_rng(9).integers(0, ham.dim, 300)])
+    yo = orc.apply_rows_rng(N, N // 2, bonds, J, seed, rows)
+    assert rel_l2(y[torch.from_numpy(rows).cuda()].double().cpu().numpy(), yo) <= 5e-6
+    del y
+    torch.cuda.empty_cache()
+    # FP32 vector storage (FP64-class dots) keeps this run near 30 s
+    e_u1 = ham.lanczos(max_iter=120, seed=1, storage=torch.float32)["evals"][0]
+    torch.cuda.empty_cache()
+
+    perms, chi = W.chain_dihedral(N), W.chain_dihedral_characters(N, 0, 1)
+    sym = A.Basis(N, N // 2, bonds, symmetry=(perms, chi))
+    assert sym.dim == orc.burnside_dim(N, N // 2, perms, chi) == 126068558
+    rng = np.random.default_rng(3)
+    for k in np.concatenate([[0, sym.dim - 2], rng.integers(0, sym.dim - 1, 30)]):
+        s, s2 = sym.state(int(k)), sym.state(int(k) + 1)
+        assert s < s2
+        r, u, cnt = orc.rep(N, perms, s)
+        assert r == s
+    hs = A.Hamiltonian(sym, J)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    u = torch.randn(sym.dim, dtype=torch.float64, device="cuda", generator=g)
+    v = torch.randn(sym.dim, dtype=torch.float64, device="cuda", generator=g)
+    uhv = float(torch.dot(u, hs.apply(v)))
+    vhu = float(torch.dot(v, hs.apply(u)))
+    assert abs(uhv - vhu) <= 1e-10 * abs(uhv)
+    del u, v
+    e_sym = hs.lanczos(max_iter=120, seed=1)["evals"][0]
+    assert abs(e_sym - e_u1) <= 1e-7 * abs(e_u1)
