@@ -415,6 +415,29 @@ def run_sym_chain(n: int):
     return 0
 
 
+def run_profile_case(case: str):
+    """apply8: Y = H X with eight FP32 columns on the benchmark lattice;
+    bilinear: per-bond forms <g|S_i.S_j|x> of the 56-bond ladder in FP64."""
+    import torch
+
+    from paper_2505_02901_gb300 import api, build, workloads as W
+    build.build()
+    if case == "apply8":
+        bonds, J = W.square_j1j2(LX, LY, J1, J2)
+        h = api.Hamiltonian(api.Basis(N, NUP, bonds), J)
+        x = torch.stack([api.random_vector(h.dim, SEED + c, torch.float32) for c in range(8)], 1).contiguous()
+        y = torch.empty_like(x)
+        ms = _event_time(lambda: h.apply(x, out=y), reps=3)
+        print(json.dumps({"case": case, "workload": WORKLOAD, "nvec": 8, "ms": ms}))
+    else:
+        h = api.Hamiltonian(api.Basis(28, 14, W.ladder(14, 2)), W.uniform_couplings(56, 3))
+        g = api.random_vector(h.dim, 1, torch.float64)
+        x = api.random_vector(h.dim, 2, torch.float64)
+        ms = _event_time(lambda: h.bilinear(g, x), reps=3)
+        print(json.dumps({"case": case, "workload": "14-rung ladder, 56 bonds, N=28", "ms": ms}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -426,10 +449,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only", action="store_true", help="time the headline form only")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-row measurements")
-    ap.add_argument("--case", default="bench", choices=["bench", "sym-chain"],
-                    help="sym-chain: only the symmetric product of the N-site chain with its "
-                         "translations and reflections (fully symmetric irrep), four times, for "
-                         "profiling captures (N from --chain-n)")
+    ap.add_argument("--case", default="bench", choices=["bench", "sym-chain", "apply8", "bilinear"],
+                    help="single products for profiling captures, four launches each: sym-chain, "
+                         "the symmetric product of the N-site chain with its translations and "
+                         "reflections (fully symmetric irrep, N from --chain-n); apply8, the "
+                         "eight-vector FP32 product on the --lattice block; bilinear, the per-bond "
+                         "forms of the 56-bond ladder (FP64)")
     ap.add_argument("--chain-n", type=int, default=32)
     ap.add_argument("--lattice", default="4x8",
                     help="LxxLy of the periodic J1-J2 lattice (4x8 is the benchmark; smaller "
@@ -445,6 +470,8 @@ def main():
         return run_reference(args)
     if args.case == "sym-chain":
         return run_sym_chain(args.chain_n)
+    if args.case in ("apply8", "bilinear"):
+        return run_profile_case(args.case)
 
     import numpy as np
     import torch
