@@ -193,7 +193,8 @@ def extra_rows(hbm):
     """One measurement per remaining hot-path row, each on its own workload:
     batched product (64 uneven instances, 8 FP32 right-hand sides), per-bond
     bilinear forms (14-rung ladder, FP64), symmetric products (6x6 J1-J2,
-    k=(0,0) FP64 and k=(pi/3,0) complex128), the 6x6 U(1) product in FP32
+    k=(0,0) FP64 and k=(pi/3,0) complex128; the square and triangular space
+    groups, 288 and 432 elements), the 6x6 U(1) product in FP32
     (dim 9,075,135,300), the paper's N=36 chain U(1) benchmark (product and
     steady-state Lanczos iteration, FP64 and FP32 storage), its N=36 and
     N=40 chain U(1) + lattice benchmarks (translations and reflections) and
@@ -309,6 +310,22 @@ def extra_rows(hbm):
         ms = _event_time(lambda: h.apply(x, out=y), reps=2)
         row(f"a4p_sym6x6_k{mx}0_{'c128' if basis.is_complex else 'f64'}", ms, (2 * es + 9) * basis.dim,
             dim=basis.dim, basis_build_s=build_s)
+        del basis, h, x, y
+        torch.cuda.empty_cache()
+    # next row 4: full space groups of the 36-site tori, fully symmetric irrep
+    # (translations times C4v, 288 elements; times C6v, 432 elements)
+    for lat in ("square", "triangular"):
+        bl, Jl = (b6, J6) if lat == "square" else W.triangular(6)
+        perms = W.space_group(6, 6, lat)
+        t0 = time.perf_counter()
+        basis = api.Basis(36, 18, bl, symmetry=(perms, W.space_group_characters(6, 6, lat)))
+        build_s = time.perf_counter() - t0
+        h = api.Hamiltonian(basis, Jl)
+        x = torch.randn(basis.dim, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(x)
+        ms = _event_time(lambda: h.apply(x, out=y), reps=2)
+        row(f"next4_space_group_{lat}6x6_f64", ms, (2 * 8 + 10) * basis.dim, dim=basis.dim,
+            group=len(perms), bonds=len(bl), basis_build_s=build_s, ns_per_row=ms * 1e6 / basis.dim)
         del basis, h, x, y
         torch.cuda.empty_cache()
     # 6x6 U(1) product, FP32 storage

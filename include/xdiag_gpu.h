@@ -65,9 +65,14 @@ typedef enum {
 /* A finite group of site permutations with a 1-D representation
  * (Sec. 3.9.1-3.9.2).  perms is [ngroup][N] with perms[g][i] = g(i);
  * chi_re/chi_im are the characters chi(g).  Validated: every row is a
- * permutation, the identity is present, the set is closed under
- * composition and inverses, chi is a homomorphism with |chi| = 1, and
- * the bond graph (with its couplings) is mapped onto itself. */
+ * permutation, no row is listed twice, the identity is present, the set is
+ * closed under composition and inverses, chi is a homomorphism with
+ * |chi| = 1, and the bond graph (with its couplings) is mapped onto itself.
+ * Any element order is accepted.  The orbit search is fastest when the
+ * group holds all translations of an Lx x Ly torus (site x + Lx*y, Lx <= 8):
+ * alone, or with point operations (the group is then searched coset by
+ * coset); the rotations of a ring, with or without its reflections, have a
+ * fast search too; other groups take a search over every element. */
 typedef struct {
     int ngroup;
     const int32_t *perms;
@@ -84,7 +89,7 @@ typedef struct xd_ham_s *xd_ham;
  * interaction graph `bonds` ([nb][2] site pairs, 0-based, i != j, host
  * memory).  sym == NULL gives the U(1) block.  The graph decides the index
  * layout; its couplings are set by xd_ham_create.
- * Limits: 2 <= N <= 40 for U(1) blocks, N <= 40 and ngroup <= 128 for
+ * Limits: 2 <= N <= 40 for U(1) blocks, N <= 40 and ngroup <= 2048 for
  * symmetric ones, 1 <= nb <= 4096, dim < 2^40.  Errors: XD_EINVAL,
  * XD_ERANGE, XD_ESYM, XD_ENOMEM, XD_ECUDA. */
 xd_status xd_basis_create(int N, int nup, const int32_t *bonds, int nb,

@@ -12,6 +12,8 @@
 
 #include <algorithm>
 #include <set>
+#include <string>
+#include <unordered_map>
 
 #include "xd_internal.cuh"
 
@@ -136,10 +138,17 @@ static uint64_t u1_state_host(const xd_basis_s *b, int64_t idx) {
 static xd_status check_group(const xd_basis_s *b) {
     const int N = b->N, G = b->G;
     auto P = [&](int g) { return b->perms.data() + (size_t)g * N; };
+    // permutation -> group index (the closure test is G^2 lookups)
+    std::unordered_map<std::string, int> index;
+    auto key = [&](const int32_t *p) { return std::string((const char *)p, sizeof(int32_t) * N); };
+    for (int g = G - 1; g >= 0; --g) index[key(P(g))] = g;
+    if ((int)index.size() != G) {
+        set_error("symmetry: a permutation is listed more than once");
+        return XD_ESYM;
+    }
     auto find = [&](const int32_t *p) {
-        for (int g = 0; g < G; ++g)
-            if (memcmp(P(g), p, sizeof(int32_t) * N) == 0) return g;
-        return -1;
+        auto it = index.find(key(p));
+        return it == index.end() ? -1 : it->second;
     };
     std::vector<int32_t> t(N);
     bool has_id = false;
@@ -218,6 +227,8 @@ static void free_basis(xd_basis_s *b) {
     cudaFree(b->d_minrot);
     cudaFree(b->d_amask);
     cudaFree(b->d_tg);
+    cudaFree(b->d_tpp);
+    cudaFree(b->d_pm);
     cudaFree(b->d_cg);
     cudaFree(b->d_chi);
     delete b;
@@ -256,6 +267,9 @@ xd::SymView xd_basis_s::symview() const {
     v.minrot = d_minrot;
     v.amask = d_amask;
     v.tg = d_tg;
+    v.tnp = tnp;
+    v.tpp = d_tpp;
+    v.pm = d_pm;
     v.cn = cn;
     v.cdih = cdih;
     v.cg = d_cg;

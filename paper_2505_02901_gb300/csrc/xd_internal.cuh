@@ -28,7 +28,7 @@ xd_status cuda_status(cudaError_t e, const char *what);
     } while (0)
 
 constexpr int kMaxBonds = 4096;
-constexpr int kMaxGroup = 128;
+constexpr int kMaxGroup = 2048;
 constexpr int kMaxN = 40;
 
 // ----------------------------------------------------- U(1) index layout
@@ -58,17 +58,23 @@ struct SymView {
     int N, G;
     int64_t dim;
     const uint64_t *reps;   // [dim]
-    const uint8_t *stab;    // [dim] |Stab(r)|
+    const uint16_t *stab;   // [dim] |Stab(r)|
     const ulonglong2 *rs;   // [ceil(dimU1 / 64)]: (member bits, members before the word)
     const uint64_t *act;    // [G][nchunk][256] byte tables of the action
     int nchunk;
     U1View u1;
-    // translation group of an Lx x Ly torus (site x + Lx*y), when detected:
-    // tx = Lx (0 otherwise), ty = Ly; minrot/amask: smallest rotation of an
-    // Lx-bit row and the rotations reaching it; tg[a + Lx*b] = group index
-    int tx, ty;
+    // translation group of an Lx x Ly torus (site x + Lx*y) inside the group,
+    // when detected: tx = Lx (0 otherwise), ty = Ly; minrot/amask: smallest
+    // rotation of an Lx-bit row and the rotations reaching it.  The group is
+    // the union of the cosets T p_k (k < max(1, tnp)); tpp[k] = group index of
+    // p_k, p_0 the identity; tg[k Lx Ly + a + Lx b] = group index of the
+    // element s -> T_{a,b}(p_k s).  tnp = 0: translations only.
+    int tx, ty, tnp;
     const uint8_t *minrot, *amask;
-    const int16_t *tg;
+    const int16_t *tg, *tpp;
+    // pm[(k - 1) nb + b] = p_k applied to the mask of bond b (k >= 1): the
+    // action is linear over XOR, so p_k(s ^ m) = p_k(s) ^ p_k(m)
+    const uint64_t *pm;
     // rotations of a ring (i -> i + n mod N), with or without the reflections
     // (i -> n - i mod N), when detected: cn = N (0 otherwise), cdih = 1 with
     // reflections; cg[n] = group index of rotation n, cg[N + n] of reflection n
@@ -128,13 +134,14 @@ struct xd_basis_s {
     std::vector<double> chi_re, chi_im;
     int64_t dim = 0;
     uint64_t *d_reps = nullptr;
-    uint8_t *d_stab = nullptr;
+    uint16_t *d_stab = nullptr;
     ulonglong2 *d_rs = nullptr;      // rank/select words: (bits, count before)
     uint64_t *d_act = nullptr;
     int nchunk = 0;
-    int tx = 0, ty = 0;              // detected torus translation group
+    int tx = 0, ty = 0, tnp = 0;     // detected torus translations (and their cosets)
     uint8_t *d_minrot = nullptr, *d_amask = nullptr;
-    int16_t *d_tg = nullptr;
+    int16_t *d_tg = nullptr, *d_tpp = nullptr;
+    uint64_t *d_pm = nullptr;        // point images of the bond masks
     int cn = 0, cdih = 0;            // detected ring rotations (+ reflections)
     int16_t *d_cg = nullptr;
     double *d_chi = nullptr;  // [G][2]
@@ -155,7 +162,7 @@ struct xd_ham_s {
     double *d_scal = nullptr;       // small device scalars
     double *d_lzpart = nullptr;     // Lanczos reduction partials
     int lzpart_n = 0;
-    double *d_symtab = nullptr;     // symmetric blocks: sqrt ratios [(G+1)^2] | bond orbit ids
+    double *d_symtab = nullptr;     // symmetric blocks: sqrt(a), 1/sqrt(a) [G+1 each] | bond orbit ids
     double *d_dpost = nullptr;      // block layout: postfix diagonal per L-bit word
     float *d_sp_dpost = nullptr;    // batched layout: postfix diagonal per class position
     float *d_sp_jhalf = nullptr;    // batched layout: J/2 per bond

@@ -20,6 +20,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <string>
+#include <unordered_map>
 
 #include "xd_internal.cuh"
 
@@ -76,17 +78,22 @@ __device__ __forceinline__ uint64_t torus_image(uint64_t s, int a, int b, int Lx
     return w;
 }
 
-__device__ __forceinline__ Orbit orbit_min_torus(const SymView &v, uint64_t s) {
+// Smallest top row over the translations of s: rot-minimum of one of its rows.
+__device__ __forceinline__ int torus_best(const SymView &v, uint64_t s) {
     const int Lx = v.tx, Ly = v.ty;
     const uint64_t rowmask = (1ull << Lx) - 1;
     int best = 1 << Lx;
-    for (int b = 0; b < Ly; ++b) {
-        int yt = Ly - 1 + b;
-        if (yt >= Ly) yt -= Ly;
-        const int m = __ldg(v.minrot + ((s >> (Lx * yt)) & rowmask));
-        best = min(best, m);
-    }
-    Orbit o{~0ull, 0, 0};
+    for (int y = 0; y < Ly; ++y) best = min(best, (int)__ldg(v.minrot + ((s >> (Lx * y)) & rowmask)));
+    return best;
+}
+
+// Merges into o the translation images of s whose top row is `best` (its
+// smallest top row); tg maps (a, b) to group indices.  Only the (a, b) that
+// bring a row with rot-minimum `best` to the top, rotated to it, are formed.
+__device__ __forceinline__ void torus_scan(const SymView &v, uint64_t s, int best, const int16_t *tg,
+                                           Orbit &o) {
+    const int Lx = v.tx, Ly = v.ty;
+    const uint64_t rowmask = (1ull << Lx) - 1;
     for (int b = 0; b < Ly; ++b) {
         int yt = Ly - 1 + b;
         if (yt >= Ly) yt -= Ly;
@@ -99,12 +106,56 @@ __device__ __forceinline__ Orbit orbit_min_torus(const SymView &v, uint64_t s) {
             const uint64_t w = torus_image(s, a, b, Lx, Ly, rowmask);
             if (w < o.rep) {
                 o.rep = w;
-                o.u = __ldg(v.tg + a + Lx * b);
+                o.u = __ldg(tg + a + Lx * b);
                 o.cnt = 1;
             } else if (w == o.rep) {
                 ++o.cnt;
             }
         }
+    }
+}
+
+__device__ __forceinline__ Orbit orbit_min_torus(const SymView &v, uint64_t s) {
+    Orbit o{~0ull, 0, 0};
+    torus_scan(v, s, torus_best(v, s), v.tg, o);
+    return o;
+}
+
+// Translations times point operations: G is the union of the cosets T p_k,
+// so min_G = min over k of the translation minimum of p_k s.  Only the cosets
+// whose smallest top row is the smallest of all are scanned in full.
+// w(k) returns p_k s (p_0 = identity).
+template <class W>
+__device__ __forceinline__ Orbit coset_search(const SymView &v, W w) {
+    int gb = torus_best(v, w(0));
+    uint32_t sel = 1;  // cosets reaching gb (tnp <= 32 here)
+    for (int k = 1; k < v.tnp; ++k) {
+        const int bk = torus_best(v, w(k));
+        if (bk < gb) {
+            gb = bk;
+            sel = 1u << k;
+        } else if (bk == gb) {
+            sel |= 1u << k;
+        }
+    }
+    Orbit o{~0ull, 0, 0};
+    const int T = v.tx * v.ty;
+    while (sel) {
+        const int k = __ffs(sel) - 1;
+        sel &= sel - 1;
+        torus_scan(v, w(k), gb, v.tg + k * T, o);
+    }
+    return o;
+}
+
+__device__ __forceinline__ Orbit orbit_min_cosets(const SymView &v, uint64_t s) {
+    if (v.tnp <= 32)
+        return coset_search(v, [&](int k) { return k ? act(v.act, v.nchunk, __ldg(v.tpp + k), s) : s; });
+    Orbit o{~0ull, 0, 0};
+    const int T = v.tx * v.ty;
+    for (int k = 0; k < v.tnp; ++k) {
+        const uint64_t w = k ? act(v.act, v.nchunk, __ldg(v.tpp + k), s) : s;
+        torus_scan(v, w, torus_best(v, w), v.tg + k * T, o);
     }
     return o;
 }
@@ -168,7 +219,8 @@ __device__ __forceinline__ Orbit orbit_min_ring(const SymView &v, uint64_t s) {
 }
 
 __device__ __forceinline__ Orbit orbit_min(const SymView &v, uint64_t s) {
-    return v.tx ? orbit_min_torus(v, s) : v.cn ? orbit_min_ring(v, s) : orbit_min_tables(v, s);
+    if (v.tx) return v.tnp ? orbit_min_cosets(v, s) : orbit_min_torus(v, s);
+    return v.cn ? orbit_min_ring(v, s) : orbit_min_tables(v, s);
 }
 
 __device__ __forceinline__ uint64_t find_block(const int64_t *__restrict__ hi_off, uint64_t lo,
@@ -199,12 +251,22 @@ __device__ uint64_t member_word(const SymView &v, const double *__restrict__ chi
         uint64_t s = u1_state(u, k, h);
         double cr = 0.0, ci = 0.0;
         bool is_rep = true;
-        for (int g = 0; g < v.G && is_rep; ++g) {
-            uint64_t t = act(v.act, v.nchunk, g, s);
-            if (t < s) is_rep = false;
-            if (t == s) {
-                cr += chi[2 * g];
-                ci += chi[2 * g + 1];
+        if (v.tx || v.cn) {
+            // a fast orbit search decides; the character sum runs on representatives only
+            is_rep = orbit_min(v, s).rep == s;
+            for (int g = 0; g < v.G && is_rep; ++g)
+                if (act(v.act, v.nchunk, g, s) == s) {
+                    cr += chi[2 * g];
+                    ci += chi[2 * g + 1];
+                }
+        } else {
+            for (int g = 0; g < v.G && is_rep; ++g) {
+                uint64_t t = act(v.act, v.nchunk, g, s);
+                if (t < s) is_rep = false;
+                if (t == s) {
+                    cr += chi[2 * g];
+                    ci += chi[2 * g + 1];
+                }
             }
         }
         if (is_rep && cr * cr + ci * ci > 0.25) bits |= 1ull << (k - k0);
@@ -225,7 +287,7 @@ __global__ void k_mark(SymView v, const double *__restrict__ chi, int64_t nwords
 
 __global__ void k_compact(SymView v, int64_t nwords, const uint64_t *__restrict__ bits,
                           const int64_t *__restrict__ cum, uint64_t *__restrict__ reps,
-                          uint8_t *__restrict__ stab) {
+                          uint16_t *__restrict__ stab) {
     const U1View &u = v.u1;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords;
          w += (int64_t)gridDim.x * blockDim.x) {
@@ -238,10 +300,8 @@ __global__ void k_compact(SymView v, int64_t nwords, const uint64_t *__restrict_
             int j = __ffsll((long long)b) - 1;
             b &= b - 1;
             uint64_t s = u1_state(u, k0 + j, h);
-            int c = 0;
-            for (int g = 0; g < v.G; ++g) c += act(v.act, v.nchunk, g, s) == s;
             reps[out] = s;
-            stab[out] = (uint8_t)c;
+            stab[out] = (uint16_t)orbit_min(v, s).cnt;
             ++out;
         }
     }
@@ -317,8 +377,14 @@ struct Val<true> {
     using T = double2;
 };
 
-// Row r of y = H x (see the file header).  sq[a][m] = sqrt(a / m).
-template <bool CPLX>
+// Row r of y = H x (see the file header).  sq[a] = sqrt(a), sq[G + 1 + m] =
+// 1 / sqrt(m), so sqrt(|Stab(r')| / |Stab(r)|) = sq[|Stab(r')|] sq[G + 1 + |Stab(r)|].
+// COS: translations times at most kMaxCos point operations; the point images
+// p_k s of the row are formed once and those of a flipped word by one XOR
+// with the point images of the bond masks (kept in shared memory).
+constexpr int kMaxCos = 12;
+
+template <bool CPLX, bool COS>
 __global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, const double *__restrict__ bond,
                                                         int nb, const double *__restrict__ chi,
                                                         const double *__restrict__ sq,
@@ -328,20 +394,28 @@ __global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, const double 
     uint64_t *sm_mask = (uint64_t *)smem;
     double *sm_half = (double *)(sm_mask + nb);
     double *sm_chi = sm_half + nb;          // [G][2]
-    double *sm_sq = sm_chi + 2 * v.G;       // [(G+1)^2]
+    double *sm_sq = sm_chi + 2 * v.G;       // [2 (G+1)]
+    uint64_t *sm_pm = (uint64_t *)(sm_sq + 2 * (v.G + 1));  // COS: [tnp - 1][nb]
+    uint64_t *sm_ps = sm_pm + (COS ? (v.tnp - 1) * nb : 0);   // COS: [tnp - 1][threads]
     const uint64_t *masks = (const uint64_t *)(bond + nb);
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         sm_half[b] = 0.5 * bond[b];
         sm_mask[b] = masks[b];
     }
     for (int g = threadIdx.x; g < 2 * v.G; g += blockDim.x) sm_chi[g] = chi[g];
-    for (int q = threadIdx.x; q < (v.G + 1) * (v.G + 1); q += blockDim.x) sm_sq[q] = sq[q];
+    for (int q = threadIdx.x; q < 2 * (v.G + 1); q += blockDim.x) sm_sq[q] = sq[q];
+    if constexpr (COS)
+        for (int q = threadIdx.x; q < (v.tnp - 1) * nb; q += blockDim.x) sm_pm[q] = v.pm[q];
     const double jq = bond[2 * nb];
     __syncthreads();
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < v.dim;
          r += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t s = __ldg(v.reps + r);
-        const int mr = __ldg(v.stab + r);
+        const double isr = sm_sq[v.G + 1 + __ldg(v.stab + r)];
+        if constexpr (COS) {
+            for (int k = 1; k < v.tnp; ++k)
+                sm_ps[(k - 1) * kThreads + threadIdx.x] = act(v.act, v.nchunk, __ldg(v.tpp + k), s);
+        }
         double ar = 0.0, ai = 0.0, dsub = 0.0;
         for (int b = 0; b < nb; ++b) {
             const uint64_t mk = sm_mask[b];
@@ -349,14 +423,21 @@ __global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, const double 
             if (t == 0 || t == mk) continue;
             const double hb = sm_half[b];
             dsub += hb;
-            const Orbit o = orbit_min(v, s ^ mk);
+            Orbit o;
+            if constexpr (COS) {
+                o = coset_search(v, [&](int k) {
+                    return k ? sm_ps[(k - 1) * kThreads + threadIdx.x] ^ sm_pm[(k - 1) * nb + b] : s ^ mk;
+                });
+            } else {
+                o = orbit_min(v, s ^ mk);
+            }
             const int64_t k = __ldg(v.u1.hi_off + (o.rep >> v.u1.L)) +
                               (int64_t)__ldg(v.u1.lo_rank + (o.rep & v.u1.lomask));
             const ulonglong2 wc = __ldg(v.rs + (k >> 6));
             const uint64_t word = wc.x;
             if (!((word >> (k & 63)) & 1)) continue;
             const int64_t c = (int64_t)wc.y + __popcll(word & ((1ull << (k & 63)) - 1));
-            const double a = hb * sm_sq[o.cnt * (v.G + 1) + mr];
+            const double a = hb * sm_sq[o.cnt] * isr;
             if constexpr (CPLX) {
                 const double2 xc = x[c];
                 const double cr = a * sm_chi[2 * o.u], ci = a * sm_chi[2 * o.u + 1];
@@ -426,7 +507,7 @@ __global__ void __launch_bounds__(kThreads) k_sym_bilinear(SymView v, const uint
                     if ((word >> (k & 63)) & 1) {
                         const int64_t c = (int64_t)wc.y +
                                           __popcll(word & ((1ull << (k & 63)) - 1));
-                        const double a = 0.5 * sq[o.cnt * (v.G + 1) + mr];
+                        const double a = 0.5 * sq[o.cnt] * sq[v.G + 1 + mr];
                         const double cr = a * chi[2 * o.u], ci = a * chi[2 * o.u + 1];
                         double tr, ti;
                         if constexpr (CPLX) {
@@ -488,24 +569,47 @@ static xd_status make_tables(xd_basis_s *b) {
                 tab[((size_t)g * b->nchunk + c) * 256 + val] = r;
             }
     }
-    // translation group of an Lx x Ly torus with rows of at most 8 sites?
+    // translation group of an Lx x Ly torus (rows of at most 8 sites) inside
+    // the group, and its cosets T p_k?
+    std::unordered_map<std::string, int> index;  // permutation -> group index
+    auto perm = [&](int g) { return b->perms.data() + (size_t)g * N; };
+    auto key = [&](const int32_t *q) { return std::string((const char *)q, sizeof(int32_t) * N); };
+    for (int g = 0; g < G; ++g) index.emplace(key(perm(g)), g);
     for (int Lx = 2; Lx <= 8 && !b->tx; ++Lx) {
-        if (N % Lx) continue;
-        const int Ly = N / Lx;
-        if (Lx * Ly != G) continue;
-        std::vector<int16_t> tg(G, -1);
+        if (N % Lx || G % N) continue;
+        const int Ly = N / Lx, T = N;
+        std::vector<int32_t> q(N);
+        std::vector<int> tr(T, -1);  // group index of T_{a,b}, at a + Lx b
         bool ok = true;
-        for (int g = 0; g < G && ok; ++g) {
-            const int32_t *p = b->perms.data() + (size_t)g * N;
-            const int a = p[0] % Lx, bb = p[0] / Lx;  // image of site 0 fixes (a, b)
-            for (int i = 0; i < N && ok; ++i) {
-                const int x = i % Lx, y = i / Lx;
-                ok = p[i] == ((x + a) % Lx) + Lx * ((y + bb) % Ly);
-            }
-            if (ok && tg[a + Lx * bb] >= 0) ok = false;
-            if (ok) tg[a + Lx * bb] = (int16_t)g;
+        for (int t = 0; t < T && ok; ++t) {
+            const int a = t % Lx, bb = t / Lx;
+            for (int i = 0; i < N; ++i) q[i] = ((i % Lx + a) % Lx) + Lx * ((i / Lx + bb) % Ly);
+            auto it = index.find(key(q.data()));
+            if (it == index.end()) ok = false;
+            else tr[t] = it->second;
         }
         if (!ok) continue;
+        // cosets: s -> T_{a,b}(p s) has the site map i -> p[T_{a,b}[i]]; the
+        // identity (tr[0]) is taken first so that p_0 is the identity
+        std::vector<int16_t> tg, tpp;
+        std::vector<char> covered(G, 0);
+        for (int n = -1; n < G && ok; ++n) {
+            const int g = n < 0 ? tr[0] : n;
+            if (covered[g]) continue;
+            tpp.push_back((int16_t)g);
+            for (int t = 0; t < T && ok; ++t) {
+                const int32_t *pt = perm(tr[t]);
+                for (int i = 0; i < N; ++i) q[i] = perm(g)[pt[i]];
+                auto it = index.find(key(q.data()));
+                if (it == index.end() || covered[it->second]) {
+                    ok = false;
+                } else {
+                    covered[it->second] = 1;
+                    tg.push_back((int16_t)it->second);
+                }
+            }
+        }
+        if (!ok || (int)tpp.size() * T != G) continue;
         std::vector<uint8_t> minrot(1u << Lx), amask(1u << Lx);
         for (uint32_t r = 0; r < (1u << Lx); ++r) {
             uint32_t m = r, mask = 0;
@@ -524,11 +628,27 @@ static xd_status make_tables(xd_basis_s *b) {
         XD_CUDA(cudaMalloc((void **)&b->d_minrot, minrot.size()));
         XD_CUDA(cudaMalloc((void **)&b->d_amask, amask.size()));
         XD_CUDA(cudaMalloc((void **)&b->d_tg, tg.size() * sizeof(int16_t)));
+        XD_CUDA(cudaMalloc((void **)&b->d_tpp, tpp.size() * sizeof(int16_t)));
         XD_CUDA(cudaMemcpy(b->d_minrot, minrot.data(), minrot.size(), cudaMemcpyHostToDevice));
         XD_CUDA(cudaMemcpy(b->d_amask, amask.data(), amask.size(), cudaMemcpyHostToDevice));
         XD_CUDA(cudaMemcpy(b->d_tg, tg.data(), tg.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
+        XD_CUDA(cudaMemcpy(b->d_tpp, tpp.data(), tpp.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
         b->tx = Lx;
         b->ty = Ly;
+        b->tnp = tpp.size() > 1 ? (int)tpp.size() : 0;
+        if (b->tnp) {
+            const int nb = b->nb;
+            std::vector<uint64_t> pm((size_t)(b->tnp - 1) * nb);
+            std::vector<int> inv(N);
+            for (int k = 1; k < b->tnp; ++k) {
+                const int32_t *p = perm(tpp[k]);
+                for (int i = 0; i < N; ++i) inv[p[i]] = i;  // bit j of s lands on bit inv[j]
+                for (int q = 0; q < nb; ++q)
+                    pm[(size_t)(k - 1) * nb + q] = (1ull << inv[b->bonds[q].i]) | (1ull << inv[b->bonds[q].j]);
+            }
+            XD_CUDA(cudaMalloc((void **)&b->d_pm, pm.size() * sizeof(uint64_t)));
+            XD_CUDA(cudaMemcpy(b->d_pm, pm.data(), pm.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
+        }
     }
     // rotations of a ring, with or without its reflections?
     if (!b->tx && N <= 64 && (G == N || G == 2 * N)) {
@@ -601,7 +721,7 @@ xd_status sym_build(xd_basis_s *b) {
     if (e != cudaSuccess) return cuda_status(e, "symmetric basis build");
     b->dim = total;
     XD_CUDA(cudaMalloc((void **)&b->d_reps, std::max<int64_t>(1, total) * sizeof(uint64_t)));
-    XD_CUDA(cudaMalloc((void **)&b->d_stab, std::max<int64_t>(1, total)));
+    XD_CUDA(cudaMalloc((void **)&b->d_stab, std::max<int64_t>(1, total) * sizeof(uint16_t)));
     v = b->symview();
     k_compact<<<grid, kThreads>>>(v, nwords, d_bits, d_cum, b->d_reps, b->d_stab);
     e = cudaGetLastError();
@@ -618,15 +738,18 @@ xd_status sym_build(xd_basis_s *b) {
     return XD_OK;
 }
 
-// Per-Hamiltonian tables: sqrt(a/m) for a, m in [1, G] and the orbit id of
-// every bond under the group (bilinear forms are averaged over bond orbits).
+// Per-Hamiltonian tables: sqrt(a) and 1/sqrt(a) for a in [1, G] and the
+// orbit id of every bond under the group (bilinear forms are averaged over
+// bond orbits).
 xd_status sym_ham_tables(xd_ham_s *h) {
     const xd_basis_s *b = h->b;
     const int G = b->G, nb = b->nb;
-    const size_t nsq = (size_t)(G + 1) * (G + 1);
+    const size_t nsq = 2 * (size_t)(G + 1);
     std::vector<double> tab(nsq + (nb + 1) / 2 + 1, 0.0);
-    for (int a = 1; a <= G; ++a)
-        for (int m = 1; m <= G; ++m) tab[a * (G + 1) + m] = sqrt((double)a / (double)m);
+    for (int a = 1; a <= G; ++a) {
+        tab[a] = sqrt((double)a);
+        tab[G + 1 + a] = 1.0 / sqrt((double)a);
+    }
     std::vector<int32_t> orb(nb, -1);
     int norb = 0;
     for (int q = 0; q < nb; ++q) {
@@ -655,7 +778,7 @@ struct SymWork {
 
 static xd_status sym_work(const xd_ham_s *h, int grid, SymWork *w) {
     const xd_basis_s *b = h->b;
-    const size_t nsq = (size_t)(b->G + 1) * (b->G + 1);
+    const size_t nsq = 2 * (size_t)(b->G + 1);
     w->sq = h->d_symtab;
     w->orbit = (const int32_t *)(h->d_symtab + nsq);
     w->part = nullptr;
@@ -672,9 +795,11 @@ xd_status sym_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, cuda
     SymWork w;
     XD_TRY(sym_work(h, 0, &w));
     const SymView v = b->symview();
-    size_t smem = (size_t)nb * 16 + 2 * G * sizeof(double) + (size_t)(G + 1) * (G + 1) * sizeof(double);
+    size_t smem = (size_t)nb * 16 + 2 * G * sizeof(double) + 2 * (size_t)(G + 1) * sizeof(double);
+    const size_t smem_cos = smem + (size_t)std::max(0, b->tnp - 1) * (nb + kThreads) * sizeof(uint64_t);
+    int optin = 0;
     {
-        int dev = 0, optin = 0;
+        int dev = 0;
         XD_CUDA(cudaGetDevice(&dev));
         XD_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         if (smem > (size_t)optin) {
@@ -684,13 +809,16 @@ xd_status sym_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, cuda
         }
     }
     int grid = grid_for(v.dim, kThreads, 8);
+    // coset form when the point images of the bond masks fit beside the rest
+    const bool cos = v.tx && v.tnp > 1 && v.tnp <= kMaxCos && smem_cos <= std::min<size_t>(optin, 96 * 1024);
+    if (cos) smem = smem_cos;
     if (dt == XD_C128) {
-        auto kern = k_sym_apply<true>;
+        auto kern = cos ? k_sym_apply<true, true> : k_sym_apply<true, false>;
         XD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<grid, kThreads, smem, st>>>(v, h->d_bond, nb, b->d_chi, w.sq, (const double2 *)x,
                                           (double2 *)y);
     } else {
-        auto kern = k_sym_apply<false>;
+        auto kern = cos ? k_sym_apply<false, true> : k_sym_apply<false, false>;
         XD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<grid, kThreads, smem, st>>>(v, h->d_bond, nb, b->d_chi, w.sq, (const double *)x,
                                           (double *)y);

@@ -124,6 +124,79 @@ def torus_space_group(L: int) -> np.ndarray:
     return np.array(out, dtype=np.int32)
 
 
+# Point groups in lattice coordinates: generated by a rotation R of order n
+# and a mirror M, elements R^k M^e (e = 0, 1; k = 0 .. n-1), as integer 2x2
+# matrices acting on (x, y).
+POINT_GROUPS = {
+    "square": ((0, -1, 1, 0), 4, (-1, 0, 0, 1)),       # C4v: 90-degree rotation, x -> -x
+    "rectangular": ((-1, 0, 0, -1), 2, (-1, 0, 0, 1)),  # C2v: 180-degree rotation, x -> -x
+    # C6v of the triangular lattice with primitive vectors a1 = (1, 0),
+    # a2 = (1/2, sqrt(3)/2): the 60-degree rotation maps a1 -> a2 -> a2 - a1,
+    # the mirror swaps a1 and a2
+    "triangular": ((0, -1, 1, 1), 6, (0, 1, 1, 0)),
+}
+
+
+def _mat(m, x, y):
+    return m[0] * x + m[1] * y, m[2] * x + m[3] * y
+
+
+def space_group(Lx: int, Ly: int, lattice: str) -> np.ndarray:
+    """Translations times a point group on the periodic Lx x Ly lattice (site
+    x + Lx*y).  Element (e, k, b, a) = T_{a,b} R^k M^e, listed e-major, then k,
+    b, a: perms[g][i] = site of R^k M^e (x, y) + (a, b); n 2 Lx Ly elements.
+    The point operations must map the torus onto itself (Lx = Ly for the
+    square and triangular groups)."""
+    R, n, M = POINT_GROUPS[lattice]
+    if lattice != "rectangular" and Lx != Ly:
+        raise ValueError(f"the {lattice} point group needs Lx == Ly")
+    out = []
+    for e in range(2):
+        for k in range(n):
+            for b in range(Ly):
+                for a in range(Lx):
+                    row = []
+                    for i in range(Lx * Ly):
+                        x, y = i % Lx, i // Lx
+                        if e:
+                            x, y = _mat(M, x, y)
+                        for _ in range(k):
+                            x, y = _mat(R, x, y)
+                        row.append((x + a) % Lx + Lx * ((y + b) % Ly))
+                    out.append(row)
+    return np.array(out, dtype=np.int32)
+
+
+def space_group_characters(Lx: int, Ly: int, lattice: str, r: int = 1, m: int = 1,
+                           mx: int = 0, my: int = 0) -> np.ndarray:
+    """One-dimensional characters of space_group(Lx, Ly, lattice):
+    chi(T_{a,b} R^k M^e) = r^k m^e exp(i (kx a + ky b)) with r, m = +-1 and
+    momentum (kx, ky) = (2 pi mx / Lx, 2 pi my / Ly), which must be left
+    invariant by the point group (Gamma; M = (pi, pi) on the square lattice).
+    r = -1 needs an even rotation order; r = m = 1 is the fully symmetric A1."""
+    _, n, _ = POINT_GROUPS[lattice]
+    kx, ky = 2 * math.pi * mx / Lx, 2 * math.pi * my / Ly
+    out = []
+    for e in range(2):
+        for k in range(n):
+            for b in range(Ly):
+                for a in range(Lx):
+                    z = (r ** k) * (m ** e) * cmath.exp(1j * (kx * a + ky * b))
+                    out.append(complex(round(z.real, 15), round(z.imag, 15)))
+    return np.array(out, dtype=np.complex128)
+
+
+def triangular(L: int, J1: float = 1.0) -> tuple:
+    """Periodic L x L triangular lattice in the coordinates of a1 = (1, 0),
+    a2 = (1/2, sqrt(3)/2): bonds to (x+1, y), (x, y+1), (x-1, y+1), each
+    unordered pair kept once.  Returns (bonds [nb, 2] int32, J [nb])."""
+    s = lambda x, y: (x % L) + L * (y % L)  # noqa: E731
+    b = _dedupe([(s(x, y), s(x + 1, y)) for y in range(L) for x in range(L)]
+                + [(s(x, y), s(x, y + 1)) for y in range(L) for x in range(L)]
+                + [(s(x, y), s(x - 1, y + 1)) for y in range(L) for x in range(L)])
+    return np.array(b, dtype=np.int32), np.full(len(b), J1)
+
+
 def torus_translations(Lx: int, Ly: int) -> np.ndarray:
     """perms[a + Lx*b][i] = site of (x+a, y+b) for i = (x, y)."""
     out = []

@@ -149,3 +149,52 @@ def test_paper_chain36_u1_and_dihedral_sector(orc):
     del u, v
     e_sym = hs.lanczos(max_iter=120, seed=1)["evals"][0]
     assert abs(e_sym - e_u1) <= 1e-7 * abs(e_u1)
+
+
+def test_space_groups_6x6_full_size(orc):
+    """36-site tori at Sz = 0 with their full space groups: 288 elements on
+    the square lattice, 432 on the triangular one (coset orbit search).
+    Burnside dimensions, sampled representatives valid and ascending with
+    their stabilisers, Hermiticity, and for the square Heisenberg model
+    (J2 = 0) the lowest level of the fully symmetric block equal to the lowest
+    level of the k = 0 translation block: with N/2 = 18 even the ground state
+    is invariant under translations, and the point operations that keep the
+    sublattices (all of them here) fix it by the Marshall sign rule."""
+    A = api()
+    for lattice in ("square", "triangular"):
+        if lattice == "square":
+            bonds, _ = W.square_j1j2(6, 6)
+            bonds = bonds[:72]  # nearest neighbours only
+        else:
+            bonds, _ = W.triangular(6)
+        J = np.ones(len(bonds))
+        perms = W.space_group(6, 6, lattice)
+        chi = W.space_group_characters(6, 6, lattice)
+        sym = A.Basis(36, 18, bonds, symmetry=(perms, chi))
+        assert sym.dim == orc.burnside_dim(36, 18, perms, chi)
+        rng = np.random.default_rng(len(perms))
+        for k in np.concatenate([[0, sym.dim - 2], rng.integers(0, sym.dim - 1, 25)]):
+            s, s2 = sym.state(int(k)), sym.state(int(k) + 1)
+            assert s < s2
+            r, u, cnt = orc.rep(36, perms, s)
+            assert r == s
+            stab = [g for g in range(len(perms)) if orc.act(36, perms[g], s) == s]
+            assert abs(sum(chi[g] for g in stab)) > 0.5 and len(stab) == cnt
+            assert sym.index(s) == k
+        hs = A.Hamiltonian(sym, J)
+        g = torch.Generator(device="cuda").manual_seed(len(perms))
+        u = torch.randn(sym.dim, dtype=torch.float64, device="cuda", generator=g)
+        v = torch.randn(sym.dim, dtype=torch.float64, device="cuda", generator=g)
+        uhv = float(torch.dot(u, hs.apply(v)))
+        vhu = float(torch.dot(v, hs.apply(u)))
+        assert abs(uhv - vhu) <= 1e-10 * abs(uhv)
+        del u, v
+        if lattice == "square":
+            e_sg = hs.lanczos(max_iter=110, seed=1)["evals"][0]
+            del hs, sym
+            tperms, tchi = W.torus_translations(6, 6), W.torus_characters(6, 6, 0, 0)
+            ht = A.Hamiltonian(A.Basis(36, 18, bonds, symmetry=(tperms, tchi)), J)
+            e_t = ht.lanczos(max_iter=110, seed=1)["evals"][0]
+            del ht
+            assert abs(e_sg - e_t) <= 1e-9 * abs(e_t)
+        torch.cuda.empty_cache()

@@ -25,7 +25,7 @@ def _dihedral(N, m, parity):
 
 
 def _space_group(L):
-    # 8 L^2 group elements: 128 at L = 4, the largest group the library takes
+    # 8 L^2 group elements (128 at L = 4)
     b, J = W.square_j1j2(L, L)
     g = W.torus_space_group(L)
     return L * L, b, J, g, np.ones(len(g), dtype=np.complex128)
@@ -116,3 +116,102 @@ def test_sym_errors(orc):
     with pytest.raises(XDError) as e:  # couplings not invariant
         A.Hamiltonian(b, np.arange(8.0))
     assert e.value.status == XD_ESYM
+
+
+def _wide(Lx, Ly, lattice, r, m, mx=0, my=0):
+    if lattice == "triangular":
+        b, J = W.triangular(Lx)
+    else:
+        b, J = W.square_j1j2(Lx, Ly)
+    return (Lx * Ly, b, J, W.space_group(Lx, Ly, lattice),
+            W.space_group_characters(Lx, Ly, lattice, r, m, mx, my))
+
+
+def _mirror_translations(Lx, Ly, m, my):
+    """Translations times the single mirror x -> -x (elements R^0 M^e of the
+    rectangular group): every ky is invariant, so the characters are complex."""
+    b, J = W.square_j1j2(Lx, Ly)
+    g = W.space_group(Lx, Ly, "rectangular")
+    c = W.space_group_characters(Lx, Ly, "rectangular", 1, m, 0, my)
+    T = Lx * Ly
+    rows = np.r_[0:T, 2 * T:3 * T]
+    return Lx * Ly, b, J, g[rows], c[rows]
+
+
+def _scrambled(case, seed):
+    N, b, J, g, c = case
+    p = np.random.default_rng(seed).permutation(len(g))
+    return N, b, J, g[p], c[p]
+
+
+# (case, sectors): 96 to 432 group elements, translations times C2v, C4v, C6v
+WIDE = [
+    (_wide(3, 3, "triangular", 1, 1), (3, 4, 5)),
+    (_wide(3, 3, "triangular", -1, -1), (4,)),
+    (_wide(4, 4, "triangular", 1, -1), (5, 6)),
+    (_wide(3, 4, "rectangular", -1, 1, 0, 2), (5, 6)),
+    (_wide(4, 6, "rectangular", 1, 1, 2, 3), (4,)),
+    (_wide(5, 5, "square", -1, 1), (4,)),
+    (_wide(6, 6, "square", 1, 1), (3, 4)),
+    (_wide(6, 6, "square", -1, -1, 3, 3), (4,)),
+    (_wide(6, 6, "triangular", 1, 1), (3,)),
+    (_mirror_translations(4, 6, -1, 1), (4, 5)),
+    (_scrambled(_wide(4, 4, "triangular", 1, 1), 3), (5,)),
+    (_scrambled(_mirror_translations(3, 4, 1, 1), 5), (6,)),
+]
+
+
+@pytest.mark.parametrize("case", range(len(WIDE)))
+def test_wide_groups_basis_and_apply(orc, case):
+    """Space groups beyond 128 elements take the translation-coset orbit
+    search: representatives, |Stab| through the products, and y = H x match the
+    oracle's plain search over every group element."""
+    A = api()
+    (N, bonds, J, perms, chi), sectors = WIDE[case]
+    for nup in sectors:
+        blk = orc.SymBlock(N, nup, perms, chi)
+        basis = A.Basis(N, nup, bonds, symmetry=(perms, chi))
+        assert basis.dim == blk.dim == orc.burnside_dim(N, nup, perms, chi)
+        if blk.dim == 0:
+            continue
+        got = np.array([basis.state(k) for k in range(blk.dim)], dtype=np.uint64)
+        assert np.array_equal(got, blk.reps)
+        ham = A.Hamiltonian(basis, J)
+        rng = np.random.default_rng(case * 10 + nup)
+        if basis.is_complex:
+            x = rng.standard_normal(blk.dim) + 1j * rng.standard_normal(blk.dim)
+            y = ham.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+        else:
+            x = rng.standard_normal(blk.dim)
+            y = ham.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+        yo = blk.apply(bonds, J, x)
+        if not basis.is_complex:
+            assert np.abs(yo.imag).max() < 1e-13
+            yo = yo.real
+        assert rel_l2(y, yo) <= 1e-12
+
+
+def test_wide_group_bilinear_and_limit(orc):
+    """Bond forms on a 192-element block against the oracle's U(1) forms of
+    the lifted vectors, and the group-size limit."""
+    A = api()
+    from paper_2505_02901_gb300._lib import XDError
+    N, bonds, J, perms, chi = _wide(4, 4, "triangular", 1, 1)
+    nup = 6
+    blk = orc.SymBlock(N, nup, perms, chi)
+    basis = A.Basis(N, nup, bonds, symmetry=(perms, chi))
+    ham = A.Hamiltonian(basis, J)
+    rng = np.random.default_rng(11)
+    g = rng.standard_normal(blk.dim)
+    x = rng.standard_normal(blk.dim)
+    st = orc.enumerate_states(N, nup)
+    B = blk.lift(st)
+    want = orc.bond_forms(N, st, bonds, (B @ g).real, (B @ x).real)
+    # within a one-dimensional irrep the form is constant on each bond orbit
+    # (one orbit here: every bond of the triangular lattice)
+    assert np.ptp(want) < 1e-11 * max(1.0, np.abs(want).max())
+    got = ham.bilinear(torch.from_numpy(g).cuda(), torch.from_numpy(x).cuda()).cpu().numpy()
+    assert np.abs(got - want).max() < 1e-11 * max(1.0, np.abs(want).max())
+    big = np.tile(perms, (11, 1))[:2049]
+    with pytest.raises(XDError):
+        A.Basis(N, nup, bonds, symmetry=(big, np.ones(len(big), dtype=np.complex128)))

@@ -191,3 +191,64 @@ def test_dihedral_chain36_dimension(orc):
     d40 = orc.burnside_dim(40, 20, W.chain_dihedral(40), W.chain_dihedral_characters(40, 0, 1))
     assert d40 == 1723176308
     assert abs(d40 - 1.7e9) / 1.7e9 < 0.05
+
+
+SPACE_GROUPS = [(3, 3, "triangular", 4), (4, 4, "triangular", 5), (3, 4, "rectangular", 6),
+                (4, 6, "rectangular", 3), (5, 5, "square", 3)]
+
+
+@pytest.mark.parametrize("Lx,Ly,lattice,nup", SPACE_GROUPS)
+def test_space_group_blocks_are_projections(orc, Lx, Ly, lattice, nup):
+    """Translations times the point group (C6v, C2v, C4v; 108 to 200 elements)
+    at Gamma, all four one-dimensional irreps: the block is the projection of
+    the U(1) block (orthonormal lifted columns, product equal to the projected
+    U(1) product on random vectors) and every eigenvector of the block lifts to
+    an eigenvector of the U(1) Hamiltonian with the same energy."""
+    N = Lx * Ly
+    if lattice == "triangular":
+        bonds, J = W.triangular(Lx)
+    else:
+        bonds, J = W.square_j1j2(Lx, Ly)
+    perms = W.space_group(Lx, Ly, lattice)
+    st = orc.enumerate_states(N, nup)
+    rng = np.random.default_rng(N)
+    total = 0
+    for r in (1, -1):
+        for m in (1, -1):
+            chi = W.space_group_characters(Lx, Ly, lattice, r, m)
+            blk = orc.SymBlock(N, nup, perms, chi)
+            assert blk.dim == orc.burnside_dim(N, nup, perms, chi)
+            total += blk.dim
+            if blk.dim == 0:
+                continue
+            B = blk.lift(st)
+            assert np.abs(B.conj().T @ B - np.eye(blk.dim)).max() < 1e-13
+            for _ in range(2):
+                x = rng.standard_normal(blk.dim) + 1j * rng.standard_normal(blk.dim)
+                Bx = B @ x
+                hx = orc.apply_u1(N, st, bonds, J, Bx.real) + 1j * orc.apply_u1(N, st, bonds, J, Bx.imag)
+                assert np.abs(blk.apply(bonds, J, x) - B.conj().T @ hx).max() < 1e-12
+            Hk = blk.dense(bonds, J)
+            assert np.abs(Hk - Hk.conj().T).max() < 1e-13
+            w, V = np.linalg.eigh(Hk)
+            for k in range(min(3, blk.dim)):
+                psi = B @ V[:, k]
+                hp = orc.apply_u1(N, st, bonds, J, psi.real) + 1j * orc.apply_u1(N, st, bonds, J, psi.imag)
+                assert np.abs(hp - w[k] * psi).max() < 1e-11
+    assert 0 < total <= math.comb(N, nup)
+
+
+def test_space_group_6x6_dimensions(orc):
+    """Burnside dimensions of the 288-element square and 432-element
+    triangular space groups of the 36-site tori at Sz = 0, trivial irrep: the
+    two blocks are about 1/|G| of C(36, 18), and the 2-d irreps keep the
+    one-dimensional blocks of the square group short of the full count."""
+    sq = W.space_group(6, 6, "square")
+    tri = W.space_group(6, 6, "triangular")
+    d_sq = orc.burnside_dim(36, 18, sq, W.space_group_characters(6, 6, "square"))
+    d_tri = orc.burnside_dim(36, 18, tri, W.space_group_characters(6, 6, "triangular"))
+    full = math.comb(36, 18)
+    assert abs(d_sq * 288 / full - 1) < 0.01 and abs(d_tri * 432 / full - 1) < 0.01
+    gamma = sum(orc.burnside_dim(36, 18, sq, W.space_group_characters(6, 6, "square", r, m))
+                for r in (1, -1) for m in (1, -1))
+    assert gamma < orc.burnside_dim(36, 18, W.torus_translations(6, 6), W.torus_characters(6, 6, 0, 0))
