@@ -41,6 +41,8 @@ FORM_NOTE = {
 TRAFFIC = {"f32": 71.64e9, "f64": 146.00e9}
 # the kernel each form's product runs at this workload
 KERNEL = {"f32": "k_spmm<12>", "f64": "k_block_apply<double, 16, 1>"}
+# GB300 HBM3e nominal bandwidth (the measured copy bandwidth is the peak used)
+HBM_NOMINAL_GBS = 7900.0
 
 
 class _Null:
@@ -126,22 +128,50 @@ def cpu_baseline(seconds: float = 12.0):
     bonds, J = W.square_j1j2(LX, LY, J1, J2)
     dim = math.comb(N, NUP)
     rng = np.random.default_rng(0)
-    cores = os.cpu_count() or 1
-    n, t_used, total_rows = 64 * cores, 0.0, 0
-    while t_used < seconds:
-        rows = rng.integers(0, dim, n)
-        t0 = time.perf_counter()
-        oracle.apply_rows_rng(N, NUP, bonds, J, SEED, rows)
-        dt = time.perf_counter() - t0
-        t_used += dt
-        total_rows += n
-        if dt < seconds / 4:
-            n *= 2
-    rows_per_s = total_rows / t_used
     el_per_row = elements_per_matvec(bonds) / dim
-    return {"value": rows_per_s * el_per_row, "unit": "elements/s", "cores": cores, "kind": "oracle",
+
+    def rate(budget, n):
+        t_used, total = 0.0, 0
+        while t_used < budget:
+            rows = rng.integers(0, dim, n)
+            t0 = time.perf_counter()
+            oracle.apply_rows_rng(N, NUP, bonds, J, SEED, rows)
+            dt = time.perf_counter() - t0
+            t_used += dt
+            total += n
+            if dt < budget / 4:
+                n *= 2
+        return total, t_used
+
+    cores = oracle.threads()
+    total_rows, t_used = rate(seconds, 64 * cores)
+    # one thread on a smaller sample of the same rows, for the per-core rate
+    oracle.threads(1)
+    try:
+        rows1, t1 = rate(max(1.0, seconds / 6), 256)
+    finally:
+        oracle.threads(cores)
+    return {"value": total_rows / t_used * el_per_row, "unit": "elements/s", "cores": cores, "kind": "oracle",
+            "single_core_value": rows1 / t1 * el_per_row, "host": _host_cpu(),
             "sample": f"{total_rows} random rows of the N=32 block, x from the seeded generator, "
-                      f"{t_used:.1f} s (OpenMP over rows)"}
+                      f"{t_used:.1f} s (OpenMP over rows); one thread: {rows1} rows, {t1:.1f} s"}
+
+
+def _host_cpu() -> str:
+    """Machine and CPU model of the host, as far as /proc/cpuinfo tells."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                key = ln.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "cpu implementer") and ":" in ln:
+                    model = (model + " " if model else "") + key + "=" + ln.split(":", 1)[1].strip()
+                    if key == "model name" or model.count("=") >= 2:
+                        break
+    except OSError:
+        pass
+    return f"{platform.machine()} {os.cpu_count()} cpus {model}".strip()
 
 
 def _event_time(fn, reps=3):
@@ -624,6 +654,8 @@ def main():
         "roofline": {"bound": "hbm", "achieved": fh["hbm_gbs_compulsory"], "peak": hbm, "unit": "GB/s",
                      "frac": fh["roofline_frac"], "traffic": TRAFFIC.get(head),
                      "kernel": KERNEL[head], "peak_kind": peak_kind,
+                     "frac_of_nominal": fh["hbm_gbs_compulsory"] / HBM_NOMINAL_GBS,
+                     "nominal_peak": HBM_NOMINAL_GBS,
                      "note": f"achieved = compulsory 2*{esize}*dim bytes per H.v / mean launch time"},
         "forms": forms,
         "clocks": clk.summary(),

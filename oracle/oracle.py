@@ -60,6 +60,7 @@ _i32, _i64, _u64 = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64
 
 def _declare(L):
     sig = {
+        "xo_threads": (_i32, [_i32]),
         "xo_binom": (_i64, [_i32, _i32]),
         "xo_popcount": (_i32, [_u64]),
         "xo_enumerate": (_i64, [_i32, _i32, _u64p]),
@@ -101,6 +102,12 @@ def _f64(a):
 
 
 # ------------------------------------------------------------------ basis
+def threads(n: int = 0) -> int:
+    """Threads of the oracle's OpenMP loops; n >= 1 sets them.  Returns the
+    count in force."""
+    return int(lib().xo_threads(n))
+
+
 def binom(n: int, k: int) -> int:
     return int(lib().xo_binom(n, k))
 

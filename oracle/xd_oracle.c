@@ -28,6 +28,23 @@
 
 #include "xd_oracle.h"
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads used by the OpenMP loops below (always 1 without OpenMP); n >= 1
+ * sets it.  Returns the count in force afterwards. */
+int xo_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* ---------------------------------------------------------------- basics */
 
 int64_t xo_binom(int n, int k)

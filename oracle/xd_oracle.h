@@ -3,6 +3,7 @@
 #define XD_ORACLE_H
 #include <stdint.h>
 
+int xo_threads(int n);
 int64_t xo_binom(int n, int k);
 int xo_popcount(uint64_t s);
 int64_t xo_enumerate(int N, int nup, uint64_t *out);

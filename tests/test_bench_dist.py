@@ -54,3 +54,19 @@ def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(12.5) == 12.5
     assert bench.whole_job_rate(1, 3.0e9, 1000.0) == pytest.approx(3.0e9)
+
+
+def test_cpu_baseline_threads_and_single_core():
+    """The CPU-baseline leg reports the oracle's thread count, a one-thread
+    rate below the all-thread one (or equal on one core), and leaves the
+    oracle's thread count as it found it."""
+    import bench
+    from oracle import oracle as orc
+    before = orc.threads()
+    r = bench.cpu_baseline(seconds=1.0)
+    assert orc.threads() == before == r["cores"]
+    assert r["kind"] == "oracle" and r["value"] > 0 and r["single_core_value"] > 0
+    if r["cores"] > 1:
+        assert r["single_core_value"] < r["value"]
+    assert orc.threads(1) == 1
+    orc.threads(before)
