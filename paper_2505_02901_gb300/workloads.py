@@ -197,6 +197,31 @@ def triangular(L: int, J1: float = 1.0) -> tuple:
     return np.array(b, dtype=np.int32), np.full(len(b), J1)
 
 
+def shastry_sutherland(Lx: int, Ly: int, J: float = 1.0, Jp: float = 0.5):
+    """Shastry-Sutherland lattice on the periodic Lx x Ly square lattice (Lx,
+    Ly even), the model of the paper's thermal pure quantum state example
+    (Sec. 4): nearest-neighbour bonds J' and orthogonal dimers J on half of
+    the plaquette diagonals, (x, y)-(x+1, y+1) for x, y even and
+    (x+1, y)-(x, y+1) for x, y odd, so that every site is in one dimer.
+    Returns (bonds [nb, 2] int32, J [nb], dimers [N/2, 2] int32); the dimer
+    bonds come first."""
+    if Lx % 2 or Ly % 2 or Lx < 4 or Ly < 4:
+        raise ValueError("the Shastry-Sutherland pattern needs even Lx, Ly >= 4")
+    s = lambda x, y: (x % Lx) + Lx * (y % Ly)  # noqa: E731
+    dim = []
+    for y in range(Ly):
+        for x in range(Lx):
+            if x % 2 == 0 and y % 2 == 0:
+                dim.append((s(x, y), s(x + 1, y + 1)))
+            elif x % 2 == 1 and y % 2 == 1:
+                dim.append((s(x + 1, y), s(x, y + 1)))
+    nn = _dedupe([(s(x, y), s(x + 1, y)) for y in range(Ly) for x in range(Lx)]
+                 + [(s(x, y), s(x, y + 1)) for y in range(Ly) for x in range(Lx)])
+    bonds = np.array(dim + nn, dtype=np.int32)
+    Jb = np.array([J] * len(dim) + [Jp] * len(nn), dtype=np.float64)
+    return bonds, Jb, np.array(dim, dtype=np.int32)
+
+
 def torus_translations(Lx: int, Ly: int) -> np.ndarray:
     """perms[a + Lx*b][i] = site of (x+a, y+b) for i = (x, y)."""
     out = []
