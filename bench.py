@@ -338,7 +338,7 @@ def extra_rows(hbm):
         x = torch.randn(basis.dim, dtype=dt, device="cuda")
         y = torch.empty_like(x)
         ms = _event_time(lambda: h.apply(x, out=y), reps=2)
-        row(f"a4p_sym6x6_k{mx}0_{'c128' if basis.is_complex else 'f64'}", ms, (2 * es + 9) * basis.dim,
+        row(f"a4p_sym6x6_k{mx}0_{'c128' if basis.is_complex else 'f64'}", ms, (2 * es + 10) * basis.dim,
             dim=basis.dim, basis_build_s=build_s)
         del basis, h, x, y
         torch.cuda.empty_cache()
@@ -398,7 +398,7 @@ def extra_rows(hbm):
         ms = _event_time(lambda: h.apply(x, out=y), reps=2)
         del x, y
         torch.cuda.empty_cache()
-        row(f"paper_chain{Nc}_lattice_f64", ms, (2 * 8 + 9) * basis.dim, dim=basis.dim, group=2 * Nc,
+        row(f"paper_chain{Nc}_lattice_f64", ms, (2 * 8 + 10) * basis.dim, dim=basis.dim, group=2 * Nc,
             basis_build_s=build_s, lanczos_s_per_iter=_lanczos_steady(h, torch.float64, 3),
             paper_fp64_s_per_iter=paper_s, paper_hardware="64 OpenMP threads, Xeon Platinum 8360Y")
         del basis, h
