@@ -35,6 +35,16 @@ def chain(N: int) -> np.ndarray:
     return np.array(_dedupe([(i, (i + 1) % N) for i in range(N)]), dtype=np.int32)
 
 
+def chain_j1j2(N: int, J1: float = 1.0, J2: float = 0.5):
+    """Periodic chain with nearest (J1) and next-nearest (J2) neighbour bonds,
+    J1 bonds (i, i+1) first, then (i, i+2).  J2 = J1/2 is the Majumdar-Ghosh
+    point.  Returns (bonds [2N, 2] int32, J [2N])."""
+    if N < 5:
+        raise ValueError("the J1-J2 chain needs N >= 5 for distinct bonds")
+    b = [(i, (i + 1) % N) for i in range(N)] + [(i, (i + 2) % N) for i in range(N)]
+    return np.array(b, dtype=np.int32), np.array([J1] * N + [J2] * N, dtype=np.float64)
+
+
 def ladder(L: int, rung_copies: int = 2) -> np.ndarray:
     """Two-leg periodic ladder on the L x 2 lattice (leg y=0 is sites 0..L-1,
     leg y=1 is sites L..2L-1).  Bond order: leg 0 (i, i+1), leg 1, then the
