@@ -462,6 +462,26 @@ def run_sym_chain(n: int):
     return 0
 
 
+def run_space_group(lattice: str, nup: int):
+    """The symmetric product on the 36-site torus with its full space group
+    (square: translations x C4v, 288 elements, J1-J2; triangular:
+    translations x C6v, 432 elements), fully symmetric irrep, four times."""
+    import torch
+
+    from paper_2505_02901_gb300 import api, build, workloads as W
+    build.build()
+    bonds, J = W.square_j1j2(6, 6) if lattice == "square" else W.triangular(6)
+    perms = W.space_group(6, 6, lattice)
+    basis = api.Basis(36, nup, bonds, symmetry=(perms, W.space_group_characters(6, 6, lattice)))
+    h = api.Hamiltonian(basis, J)
+    x = api.random_vector(basis.dim, SEED, torch.float64)
+    y = torch.empty_like(x)
+    ms = _event_time(lambda: h.apply(x, out=y), reps=3)
+    print(json.dumps({"case": "space-group", "lattice": lattice, "nup": nup, "group": len(perms),
+                      "dim": basis.dim, "ms": ms}))
+    return 0
+
+
 def run_profile_case(case: str):
     """apply8: Y = H X with eight FP32 columns on the benchmark lattice;
     bilinear: per-bond forms <g|S_i.S_j|x> of the 56-bond ladder in FP64."""
@@ -496,13 +516,18 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only", action="store_true", help="time the headline form only")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-row measurements")
-    ap.add_argument("--case", default="bench", choices=["bench", "sym-chain", "apply8", "bilinear"],
+    ap.add_argument("--case", default="bench",
+                    choices=["bench", "sym-chain", "space-group", "apply8", "bilinear"],
                     help="single products for profiling captures, four launches each: sym-chain, "
                          "the symmetric product of the N-site chain with its translations and "
-                         "reflections (fully symmetric irrep, N from --chain-n); apply8, the "
+                         "reflections (fully symmetric irrep, N from --chain-n); space-group, the "
+                         "symmetric product of the 36-site torus with its full space group "
+                         "(--group square or triangular, --nup); apply8, the "
                          "eight-vector FP32 product on the --lattice block; bilinear, the per-bond "
                          "forms of the 56-bond ladder (FP64)")
     ap.add_argument("--chain-n", type=int, default=32)
+    ap.add_argument("--group", default="square", choices=["square", "triangular"])
+    ap.add_argument("--nup", type=int, default=18)
     ap.add_argument("--lattice", default="4x8",
                     help="LxxLy of the periodic J1-J2 lattice (4x8 is the benchmark; smaller "
                          "ones serve ncu captures, e.g. 4x7)")
@@ -517,6 +542,8 @@ def main():
         return run_reference(args)
     if args.case == "sym-chain":
         return run_sym_chain(args.chain_n)
+    if args.case == "space-group":
+        return run_space_group(args.group, args.nup)
     if args.case in ("apply8", "bilinear"):
         return run_profile_case(args.case)
 
