@@ -145,6 +145,14 @@ def cpu_baseline(seconds: float = 12.0):
 
     cores = oracle.threads()
     total_rows, t_used = rate(seconds, 64 * cores)
+    # the oracle's Lanczos (FP64, full reorthogonalisation) on the N=16 chain,
+    # Sz=0 (dim 12,870), 100 steps, as context for the device's iteration time
+    st16 = oracle.enumerate_states(16, 8)
+    b16 = W.chain(16)
+    t0 = time.perf_counter()
+    a16, _ = oracle.lanczos(lambda v: oracle.apply_u1(16, st16, b16, [1.0] * 16, v), st16.size,
+                            oracle.rng_normal(SEED, 0, st16.size), 100)
+    lz16 = (time.perf_counter() - t0) / len(a16)
     # one thread on a smaller sample of the same rows, for the per-core rate
     oracle.threads(1)
     try:
@@ -153,6 +161,7 @@ def cpu_baseline(seconds: float = 12.0):
         oracle.threads(cores)
     return {"value": total_rows / t_used * el_per_row, "unit": "elements/s", "cores": cores, "kind": "oracle",
             "single_core_value": rows1 / t1 * el_per_row, "host": _host_cpu(),
+            "lanczos_chain16_s_per_iter": lz16,
             "sample": f"{total_rows} random rows of the N=32 block, x from the seeded generator, "
                       f"{t_used:.1f} s (OpenMP over rows); one thread: {rows1} rows, {t1:.1f} s"}
 
