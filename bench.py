@@ -118,9 +118,11 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.samples)}
 
 
-def cpu_baseline(seconds: float = 12.0):
+def cpu_baseline(seconds: float = 12.0, extras: bool = True):
     """The oracle's sampled-row product (counting index, no stored list) on
-    the host cores, on a bounded random sample of rows of this workload."""
+    the host cores, on a bounded random sample of rows of this workload;
+    with extras, also its one-thread rate and its Lanczos iteration on the
+    N=16 chain."""
     import numpy as np
 
     import oracle
@@ -145,6 +147,12 @@ def cpu_baseline(seconds: float = 12.0):
 
     cores = oracle.threads()
     total_rows, t_used = rate(seconds, 64 * cores)
+    out = {"value": total_rows / t_used * el_per_row, "unit": "elements/s", "cores": cores, "kind": "oracle",
+           "host": _host_cpu(),
+           "sample": f"{total_rows} random rows of the N=32 block, x from the seeded generator, "
+                     f"{t_used:.1f} s (OpenMP over rows)"}
+    if not extras:
+        return out
     # the oracle's Lanczos (FP64, full reorthogonalisation) on the N=16 chain,
     # Sz=0 (dim 12,870), 100 steps, as context for the device's iteration time
     st16 = oracle.enumerate_states(16, 8)
@@ -159,11 +167,9 @@ def cpu_baseline(seconds: float = 12.0):
         rows1, t1 = rate(max(1.0, seconds / 6), 256)
     finally:
         oracle.threads(cores)
-    return {"value": total_rows / t_used * el_per_row, "unit": "elements/s", "cores": cores, "kind": "oracle",
-            "single_core_value": rows1 / t1 * el_per_row, "host": _host_cpu(),
-            "lanczos_chain16_s_per_iter": lz16,
-            "sample": f"{total_rows} random rows of the N=32 block, x from the seeded generator, "
-                      f"{t_used:.1f} s (OpenMP over rows); one thread: {rows1} rows, {t1:.1f} s"}
+    out.update({"single_core_value": rows1 / t1 * el_per_row, "lanczos_chain16_s_per_iter": lz16})
+    out["sample"] += f"; one thread: {rows1} rows, {t1:.1f} s"
+    return out
 
 
 def _host_cpu() -> str:
@@ -433,8 +439,8 @@ def run_reference(args):
     bonds, _ = W.square_j1j2(LX, LY, J1, J2)
     per_step = min(10.0, max(1.0, 60.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        cpu_baseline(seconds=per_step)
-    rates = [cpu_baseline(seconds=per_step) for _ in range(max(1, args.steps))]
+        cpu_baseline(seconds=per_step, extras=False)
+    rates = [cpu_baseline(seconds=per_step, extras=k == args.steps - 1) for k in range(max(1, args.steps))]
     value = statistics.mean(r["value"] for r in rates)
     elements = elements_per_matvec(bonds)
     cb = dict(rates[-1])
