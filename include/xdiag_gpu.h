@@ -261,6 +261,13 @@ const char *xd_last_error(void);
 /* Library version string. */
 const char *xd_version(void);
 
+/* Failure injection for testing error paths on the host: with n >= 0 the
+ * library's next n device allocations succeed and the one after fails as an
+ * out-of-memory error (the call that made it returns XD_ENOMEM, releasing
+ * what it had allocated); the injection then switches itself off.  n < 0
+ * switches it off at once.  Process-wide; always returns XD_OK. */
+xd_status xd_debug_fail_alloc(int64_t n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,6 +56,7 @@ SIGNATURES = {
     "xd_batch_apply": (_i, [_i, _c.POINTER(_vp), _c.POINTER(_vp), _c.POINTER(_vp), _i, _i, _vp]),
     "xd_last_error": (_c.c_char_p, []),
     "xd_version": (_c.c_char_p, []),
+    "xd_debug_fail_alloc": (_i, [_i64]),
 }
 
 _lib = None

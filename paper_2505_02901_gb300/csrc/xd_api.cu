@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <set>
 #include <string>
 #include <unordered_map>
@@ -27,6 +28,22 @@ void set_error(const char *fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(g_err, sizeof g_err, fmt, ap);
     va_end(ap);
+}
+
+// Injected allocation failure: -1 off; n >= 0: n more allocations succeed,
+// the next one fails with cudaErrorMemoryAllocation (without allocating) and
+// the injection switches itself off.
+static std::atomic<int64_t> g_fail_after{-1};
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    int64_t n = g_fail_after.load();
+    while (n >= 0 && !g_fail_after.compare_exchange_weak(n, n - 1)) {
+    }
+    if (n == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
 }
 
 xd_status cuda_status(cudaError_t e, const char *what) {
@@ -57,7 +74,7 @@ static int popc64(uint64_t v) { return __builtin_popcountll(v); }
 
 template <typename T>
 static xd_status dcopy(T **dst, const T *src, size_t n) {
-    XD_CUDA(cudaMalloc((void **)dst, std::max<size_t>(1, n) * sizeof(T)));
+    XD_CUDA(dev_malloc((void **)dst, std::max<size_t>(1, n) * sizeof(T)));
     if (n) XD_CUDA(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
     return XD_OK;
 }
@@ -67,7 +84,7 @@ xd_status ensure_partials(xd_ham_s *h, size_t bytes) {
     if (h->d_part) cudaFree(h->d_part);
     h->d_part = nullptr;
     h->part_bytes = 0;
-    XD_CUDA(cudaMalloc((void **)&h->d_part, bytes));
+    XD_CUDA(dev_malloc((void **)&h->d_part, bytes));
     h->part_bytes = bytes;
     return XD_OK;
 }
@@ -281,6 +298,11 @@ using namespace xd;
 extern "C" {
 
 const char *xd_last_error(void) { return xd::g_err; }
+
+xd_status xd_debug_fail_alloc(int64_t n) {
+    xd::g_fail_after.store(n < 0 ? -1 : n);
+    return XD_OK;
+}
 const char *xd_version(void) { return "xdiag-gb300 0.1 (sm_103a)"; }
 
 xd_status xd_basis_create(int N, int nup, const int32_t *bonds, int nb, const xd_symmetry *sym,
@@ -464,9 +486,9 @@ xd_status xd_ham_create(xd_basis b, const double *J, xd_ham *out) {
     *out = nullptr;
     auto *h = new xd_ham_s();
     h->b = b;
-    cudaError_t e = cudaMalloc((void **)&h->d_J, sizeof(double) * b->nb);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_bond, sizeof(double) * (2 * b->nb + 1));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_scal, sizeof(double) * 64);
+    cudaError_t e = dev_malloc((void **)&h->d_J, sizeof(double) * b->nb);
+    if (e == cudaSuccess) e = dev_malloc((void **)&h->d_bond, sizeof(double) * (2 * b->nb + 1));
+    if (e == cudaSuccess) e = dev_malloc((void **)&h->d_scal, sizeof(double) * 64);
     if (e != cudaSuccess) {
         cudaFree(h->d_J);
         cudaFree(h->d_bond);

@@ -182,7 +182,7 @@ xd_status build_table(Plan *p) {
     }
     p->ntiles = tiles;
     if (h.empty()) return XD_OK;
-    if (!p->d_inst) XD_CUDA(cudaMalloc((void **)&p->d_inst, sizeof(Inst) * h.size()));
+    if (!p->d_inst) XD_CUDA(dev_malloc((void **)&p->d_inst, sizeof(Inst) * h.size()));
     XD_CUDA(cudaMemcpy(p->d_inst, h.data(), sizeof(Inst) * h.size(), cudaMemcpyHostToDevice));
     return XD_OK;
 }

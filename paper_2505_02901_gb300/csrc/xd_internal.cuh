@@ -28,6 +28,10 @@ xd_status cuda_status(cudaError_t e, const char *what);
     } while (0)
 
 constexpr int kMaxBonds = 4096;
+
+// cudaMalloc, unless an allocation failure was injected (xd_debug_fail_alloc):
+// every device allocation of the library goes through here.
+cudaError_t dev_malloc(void **p, size_t bytes);
 constexpr int kMaxGroup = 2048;
 constexpr int kMaxN = 40;
 

@@ -318,7 +318,7 @@ static xd_status ensure_lanczos_partials(xd_ham_s *h, int n) {
     cudaFree(h->d_lzpart);
     h->d_lzpart = nullptr;
     h->lzpart_n = 0;
-    XD_CUDA(cudaMalloc((void **)&h->d_lzpart, sizeof(double) * n));
+    XD_CUDA(dev_malloc((void **)&h->d_lzpart, sizeof(double) * n));
     h->lzpart_n = n;
     return XD_OK;
 }
@@ -362,7 +362,7 @@ static xd_status lanczos_run(xd_ham_s *h, int max_iter, uint64_t seed, xd_dtype 
     lw.scal = h->d_scal;
     T *buf[3] = {nullptr, nullptr, nullptr};
     for (int k = 0; k < 3; ++k) {
-        cudaError_t e = cudaMalloc((void **)&buf[k], std::max<size_t>(vbytes, 16));
+        cudaError_t e = dev_malloc((void **)&buf[k], std::max<size_t>(vbytes, 16));
         if (e != cudaSuccess) {
             for (int q = 0; q < k; ++q) cudaFree(buf[q]);
             return cuda_status(e, "cudaMalloc(Lanczos vectors)");
@@ -572,7 +572,7 @@ static xd_status evolve_run(xd_ham_s *h, const double *psi0, double zr, double z
     const size_t vbytes = (size_t)n * sizeof(double);
     double *buf[3] = {nullptr, nullptr, nullptr};
     for (int k = 0; k < 3; ++k) {
-        cudaError_t e = cudaMalloc((void **)&buf[k], std::max<size_t>(vbytes, 16));
+        cudaError_t e = dev_malloc((void **)&buf[k], std::max<size_t>(vbytes, 16));
         if (e != cudaSuccess) {
             for (int q = 0; q < k; ++q) cudaFree(buf[q]);
             return cuda_status(e, "cudaMalloc(evolution vectors)");
@@ -693,7 +693,7 @@ static xd_status ftlm_run(xd_ham_s *h, int R, int M, uint64_t seed, double *alph
     const size_t vbytes = (size_t)n * sizeof(double);
     double *buf[3] = {nullptr, nullptr, nullptr};
     for (int k = 0; k < 3; ++k) {
-        cudaError_t e = cudaMalloc((void **)&buf[k], std::max<size_t>(vbytes, 16));
+        cudaError_t e = dev_malloc((void **)&buf[k], std::max<size_t>(vbytes, 16));
         if (e != cudaSuccess) {
             for (int q = 0; q < k; ++q) cudaFree(buf[q]);
             return cuda_status(e, "cudaMalloc(FTLM vectors)");
@@ -907,7 +907,7 @@ xd_status xd_energy_grad(xd_ham h, const void *psi0, xd_dtype dt, double *dEdJ) 
     }
     const int nb = h->b->nb;
     double *d_out = nullptr;
-    XD_CUDA(cudaMalloc((void **)&d_out, sizeof(double) * nb));
+    XD_CUDA(dev_malloc((void **)&d_out, sizeof(double) * nb));
     xd_status s = xd_apply_bilinear(h, psi0, psi0, dt, d_out, nullptr);
     if (s == XD_OK) {
         cudaError_t e = cudaMemcpy(dEdJ, d_out, sizeof(double) * nb, cudaMemcpyDeviceToHost);

@@ -625,10 +625,10 @@ static xd_status make_tables(xd_basis_s *b) {
             minrot[r] = (uint8_t)m;
             amask[r] = (uint8_t)mask;
         }
-        XD_CUDA(cudaMalloc((void **)&b->d_minrot, minrot.size()));
-        XD_CUDA(cudaMalloc((void **)&b->d_amask, amask.size()));
-        XD_CUDA(cudaMalloc((void **)&b->d_tg, tg.size() * sizeof(int16_t)));
-        XD_CUDA(cudaMalloc((void **)&b->d_tpp, tpp.size() * sizeof(int16_t)));
+        XD_CUDA(dev_malloc((void **)&b->d_minrot, minrot.size()));
+        XD_CUDA(dev_malloc((void **)&b->d_amask, amask.size()));
+        XD_CUDA(dev_malloc((void **)&b->d_tg, tg.size() * sizeof(int16_t)));
+        XD_CUDA(dev_malloc((void **)&b->d_tpp, tpp.size() * sizeof(int16_t)));
         XD_CUDA(cudaMemcpy(b->d_minrot, minrot.data(), minrot.size(), cudaMemcpyHostToDevice));
         XD_CUDA(cudaMemcpy(b->d_amask, amask.data(), amask.size(), cudaMemcpyHostToDevice));
         XD_CUDA(cudaMemcpy(b->d_tg, tg.data(), tg.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
@@ -646,7 +646,7 @@ static xd_status make_tables(xd_basis_s *b) {
                 for (int q = 0; q < nb; ++q)
                     pm[(size_t)(k - 1) * nb + q] = (1ull << inv[b->bonds[q].i]) | (1ull << inv[b->bonds[q].j]);
             }
-            XD_CUDA(cudaMalloc((void **)&b->d_pm, pm.size() * sizeof(uint64_t)));
+            XD_CUDA(dev_malloc((void **)&b->d_pm, pm.size() * sizeof(uint64_t)));
             XD_CUDA(cudaMemcpy(b->d_pm, pm.data(), pm.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
         }
     }
@@ -673,20 +673,20 @@ static xd_status make_tables(xd_basis_s *b) {
             nref += cg[N + n] >= 0;
         }
         if (ok && nrot == N && (nref == 0 || nref == N) && N + nref == G) {
-            XD_CUDA(cudaMalloc((void **)&b->d_cg, cg.size() * sizeof(int16_t)));
+            XD_CUDA(dev_malloc((void **)&b->d_cg, cg.size() * sizeof(int16_t)));
             XD_CUDA(cudaMemcpy(b->d_cg, cg.data(), cg.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
             b->cn = N;
             b->cdih = nref ? 1 : 0;
         }
     }
-    XD_CUDA(cudaMalloc((void **)&b->d_act, tab.size() * sizeof(uint64_t)));
+    XD_CUDA(dev_malloc((void **)&b->d_act, tab.size() * sizeof(uint64_t)));
     XD_CUDA(cudaMemcpy(b->d_act, tab.data(), tab.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
     std::vector<double> chi(2 * G);
     for (int g = 0; g < G; ++g) {
         chi[2 * g] = b->chi_re[g];
         chi[2 * g + 1] = b->chi_im[g];
     }
-    XD_CUDA(cudaMalloc((void **)&b->d_chi, chi.size() * sizeof(double)));
+    XD_CUDA(dev_malloc((void **)&b->d_chi, chi.size() * sizeof(double)));
     XD_CUDA(cudaMemcpy(b->d_chi, chi.data(), chi.size() * sizeof(double), cudaMemcpyHostToDevice));
     return XD_OK;
 }
@@ -694,47 +694,51 @@ static xd_status make_tables(xd_basis_s *b) {
 xd_status sym_build(xd_basis_s *b) {
     XD_TRY(make_tables(b));
     const int64_t nwords = (b->dim_u1 + 63) / 64;
-    uint64_t *d_bits = nullptr;
-    int64_t *d_cum = nullptr;
-    XD_CUDA(cudaMalloc((void **)&d_bits, std::max<int64_t>(1, nwords) * sizeof(uint64_t)));
-    XD_CUDA(cudaMalloc((void **)&d_cum, (nwords + 1) * sizeof(int64_t)));
-    int64_t *cnt = nullptr, *sums = nullptr;
     const int64_t nchunks = (nwords + kScanChunk - 1) / kScanChunk;
-    XD_CUDA(cudaMalloc((void **)&cnt, std::max<int64_t>(1, nwords) * sizeof(int64_t)));
-    cudaError_t e = cudaMalloc((void **)&sums, (nchunks + 1) * sizeof(int64_t));
-    if (e != cudaSuccess) {
-        cudaFree(cnt);
-        return cuda_status(e, "cudaMalloc(scan)");
-    }
-    SymView v = b->symview();
-    int grid = grid_for(nwords, kThreads, 16);
-    k_mark<<<grid, kThreads>>>(v, b->d_chi, nwords, d_bits, cnt);
-    k_scan_sums<<<(unsigned)std::max<int64_t>(1, nchunks), kThreads>>>(cnt, nwords, sums);
-    k_scan_serial<<<1, 1>>>(sums, nchunks);
-    k_scan_apply<<<(unsigned)std::max<int64_t>(1, nchunks), kThreads>>>(cnt, nwords, sums, d_cum);
-    e = cudaGetLastError();
+    const int grid = grid_for(nwords, kThreads, 16);
+    // temporaries of the build, released on every path (the scan's as soon
+    // as the count is known, to keep the peak down)
+    uint64_t *d_bits = nullptr;
+    int64_t *d_cum = nullptr, *cnt = nullptr, *sums = nullptr;
+    const char *what = "cudaMalloc(symmetric basis build)";
+    cudaError_t e = dev_malloc((void **)&d_bits, std::max<int64_t>(1, nwords) * sizeof(uint64_t));
+    if (e == cudaSuccess) e = dev_malloc((void **)&d_cum, (nwords + 1) * sizeof(int64_t));
+    if (e == cudaSuccess) e = dev_malloc((void **)&cnt, std::max<int64_t>(1, nwords) * sizeof(int64_t));
+    if (e == cudaSuccess) e = dev_malloc((void **)&sums, (nchunks + 1) * sizeof(int64_t));
     int64_t total = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&total, sums + nchunks, sizeof total, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(d_cum + nwords, &total, sizeof total, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        what = "symmetric basis build";
+        const SymView v = b->symview();
+        k_mark<<<grid, kThreads>>>(v, b->d_chi, nwords, d_bits, cnt);
+        k_scan_sums<<<(unsigned)std::max<int64_t>(1, nchunks), kThreads>>>(cnt, nwords, sums);
+        k_scan_serial<<<1, 1>>>(sums, nchunks);
+        k_scan_apply<<<(unsigned)std::max<int64_t>(1, nchunks), kThreads>>>(cnt, nwords, sums, d_cum);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpy(&total, sums + nchunks, sizeof total, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(d_cum + nwords, &total, sizeof total, cudaMemcpyHostToDevice);
+    }
     cudaFree(cnt);
     cudaFree(sums);
-    if (e != cudaSuccess) return cuda_status(e, "symmetric basis build");
-    b->dim = total;
-    XD_CUDA(cudaMalloc((void **)&b->d_reps, std::max<int64_t>(1, total) * sizeof(uint64_t)));
-    XD_CUDA(cudaMalloc((void **)&b->d_stab, std::max<int64_t>(1, total) * sizeof(uint16_t)));
-    v = b->symview();
-    k_compact<<<grid, kThreads>>>(v, nwords, d_bits, d_cum, b->d_reps, b->d_stab);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_rs, std::max<int64_t>(1, nwords) * sizeof(ulonglong2));
     if (e == cudaSuccess) {
-        k_interleave<<<grid, kThreads>>>(nwords, d_bits, d_cum, b->d_rs);
-        e = cudaGetLastError();
+        b->dim = total;
+        what = "symmetric basis compaction";
+        e = dev_malloc((void **)&b->d_reps, std::max<int64_t>(1, total) * sizeof(uint64_t));
+        if (e == cudaSuccess) e = dev_malloc((void **)&b->d_stab, std::max<int64_t>(1, total) * sizeof(uint16_t));
+        if (e == cudaSuccess) {
+            const SymView v = b->symview();
+            k_compact<<<grid, kThreads>>>(v, nwords, d_bits, d_cum, b->d_reps, b->d_stab);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = dev_malloc((void **)&b->d_rs, std::max<int64_t>(1, nwords) * sizeof(ulonglong2));
+        if (e == cudaSuccess) {
+            k_interleave<<<grid, kThreads>>>(nwords, d_bits, d_cum, b->d_rs);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(d_bits);
     cudaFree(d_cum);
-    if (e != cudaSuccess) return cuda_status(e, "symmetric basis compaction");
-    XD_CUDA(cudaDeviceSynchronize());
+    if (e != cudaSuccess) return cuda_status(e, what);
     return XD_OK;
 }
 
@@ -765,7 +769,7 @@ xd_status sym_ham_tables(xd_ham_s *h) {
         ++norb;
     }
     memcpy(tab.data() + nsq, orb.data(), nb * sizeof(int32_t));
-    XD_CUDA(cudaMalloc((void **)&h->d_symtab, tab.size() * sizeof(double)));
+    XD_CUDA(dev_malloc((void **)&h->d_symtab, tab.size() * sizeof(double)));
     XD_CUDA(cudaMemcpy(h->d_symtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
     return XD_OK;
 }

@@ -429,9 +429,9 @@ extern "C" xd_status xd_correlations(xd_basis b, const void *psi, xd_dtype dt, c
     const int grid = grid_for(u.dim, kBT, 1);
     uint64_t *d_m = nullptr;
     double *d_part = nullptr, *d_out = nullptr;
-    cudaError_t e = cudaMalloc((void **)&d_m, sizeof(uint64_t) * npairs);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&d_part, sizeof(double) * (size_t)grid * npairs);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&d_out, sizeof(double) * npairs);
+    cudaError_t e = dev_malloc((void **)&d_m, sizeof(uint64_t) * npairs);
+    if (e == cudaSuccess) e = dev_malloc((void **)&d_part, sizeof(double) * (size_t)grid * npairs);
+    if (e == cudaSuccess) e = dev_malloc((void **)&d_out, sizeof(double) * npairs);
     if (e == cudaSuccess) e = cudaMemcpy(d_m, m.data(), sizeof(uint64_t) * npairs, cudaMemcpyHostToDevice);
     xd_status s = e == cudaSuccess ? XD_OK : cuda_status(e, "xd_correlations workspace");
     if (s == XD_OK) {

@@ -384,7 +384,7 @@ xd_status block_layout_build(xd_basis_s *b) {
     bl.maxblk = (int)binom_h(L, L / 2);
     auto up = [](auto **dst, const auto &v) -> xd_status {
         using E = typename std::remove_reference<decltype(v)>::type::value_type;
-        XD_CUDA(cudaMalloc((void **)dst, std::max<size_t>(1, v.size()) * sizeof(E)));
+        XD_CUDA(dev_malloc((void **)dst, std::max<size_t>(1, v.size()) * sizeof(E)));
         if (!v.empty()) XD_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(E), cudaMemcpyHostToDevice));
         return XD_OK;
     };
@@ -426,7 +426,7 @@ xd_status block_ham_tables(xd_ham_s *h) {
         }
         dpost[g] = d;
     }
-    if (!h->d_dpost) XD_CUDA(cudaMalloc((void **)&h->d_dpost, nlo * sizeof(double)));
+    if (!h->d_dpost) XD_CUDA(dev_malloc((void **)&h->d_dpost, nlo * sizeof(double)));
     XD_CUDA(cudaMemcpy(h->d_dpost, dpost.data(), nlo * sizeof(double), cudaMemcpyHostToDevice));
     return XD_OK;
 }

@@ -522,7 +522,7 @@ xd_status spmm_layout_build(xd_basis_s *b) {
     s.nitems = (int64_t)items.size() / kB;
     auto up = [](auto **dst, const auto &v) -> xd_status {
         using E = typename std::remove_reference<decltype(v)>::type::value_type;
-        XD_CUDA(cudaMalloc((void **)dst, std::max<size_t>(1, v.size()) * sizeof(E)));
+        XD_CUDA(dev_malloc((void **)dst, std::max<size_t>(1, v.size()) * sizeof(E)));
         if (!v.empty()) XD_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(E), cudaMemcpyHostToDevice));
         return XD_OK;
     };
@@ -540,7 +540,7 @@ xd_status spmm_layout_build(xd_basis_s *b) {
     {
         const uint64_t nh = 1ull << P;
         int64_t *cnt = nullptr;
-        XD_CUDA(cudaMalloc((void **)&cnt, (nh + 1) * sizeof(int64_t)));
+        XD_CUDA(dev_malloc((void **)&cnt, (nh + 1) * sizeof(int64_t)));
         const int grid = grid_for((int64_t)nh, 256, 16);
         k_pcsr_count<<<grid, 256>>>(P, nup, L, s.d_pre, s.npre, cnt);
         std::vector<int64_t> hc(nh + 1, 0);
@@ -560,7 +560,7 @@ xd_status spmm_layout_build(xd_basis_s *b) {
         hc[nh] = run;
         s.maxpa = (int)std::max<int64_t>(1, mx);
         e = cudaMemcpy(cnt, hc.data(), (nh + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&s.d_pcsr, std::max<int64_t>(1, run) * sizeof(uint64_t));
+        if (e == cudaSuccess) e = dev_malloc((void **)&s.d_pcsr, std::max<int64_t>(1, run) * sizeof(uint64_t));
         if (e == cudaSuccess) {
             k_pcsr_fill<<<grid, 256>>>(P, nup, L, s.d_pre, s.npre, s.d_hi_off, cnt, s.d_pcsr);
             e = cudaGetLastError();
@@ -607,8 +607,8 @@ xd_status spmm_ham_tables(xd_ham_s *h) {
         }
         dpost[g] = (float)d;
     }
-    if (!h->d_sp_dpost) XD_CUDA(cudaMalloc((void **)&h->d_sp_dpost, nlo * sizeof(float)));
-    if (!h->d_sp_jhalf) XD_CUDA(cudaMalloc((void **)&h->d_sp_jhalf, std::max(1, b->nb) * sizeof(float)));
+    if (!h->d_sp_dpost) XD_CUDA(dev_malloc((void **)&h->d_sp_dpost, nlo * sizeof(float)));
+    if (!h->d_sp_jhalf) XD_CUDA(dev_malloc((void **)&h->d_sp_jhalf, std::max(1, b->nb) * sizeof(float)));
     XD_CUDA(cudaMemcpy(h->d_sp_dpost, dpost.data(), nlo * sizeof(float), cudaMemcpyHostToDevice));
     XD_CUDA(cudaMemcpy(h->d_sp_jhalf, jhalf.data(), b->nb * sizeof(float), cudaMemcpyHostToDevice));
     double q = 0.0;

@@ -100,3 +100,17 @@ def test_wide_group_checks_run_on_the_host(L):
     # a square-lattice mirror does not map the triangular bonds onto themselves
     gs = W.space_group(6, 6, "square")
     _rejects(L, L.XD_ESYM, "bond graph", 36, 18, b, gs, np.ones(len(gs)))
+
+
+def test_injected_allocation_failure_is_an_out_of_memory_status(L):
+    """With an allocation failure injected at the first device allocation,
+    creating a valid block fails as XD_ENOMEM (on the host, before any other
+    CUDA call) and returns no handle; the injection is then off again."""
+    lib = L.lib()
+    assert lib.xd_debug_fail_alloc(0) == L.XD_OK
+    try:
+        st, h, msg = _create(L, 12, 6, W.chain(12))
+        assert st == L.XD_ENOMEM and h is None
+        assert "allocation" in msg.lower() or "memory" in msg.lower(), msg
+    finally:
+        lib.xd_debug_fail_alloc(-1)
