@@ -16,6 +16,7 @@
 #include <string>
 #include <unordered_map>
 
+#include "xd_groups.h"
 #include "xd_internal.cuh"
 
 namespace xd {
@@ -445,20 +446,11 @@ static xd_status set_J(xd_ham_s *h, const double *J) {
         }
     if (b->sym) {
         // couplings must be invariant: J of a bond equals J of its image
-        for (int g = 0; g < b->G; ++g)
-            for (int k = 0; k < b->nb; ++k) {
-                int a = b->perms[(size_t)g * b->N + b->bonds[k].i];
-                int c = b->perms[(size_t)g * b->N + b->bonds[k].j];
-                bool ok = false;
-                for (int q = 0; q < b->nb && !ok; ++q) {
-                    int u = b->bonds[q].i, v = b->bonds[q].j;
-                    if (((u == a && v == c) || (u == c && v == a)) && J[q] == J[k]) ok = true;
-                }
-                if (!ok) {
-                    set_error("couplings are not invariant under permutation %d (bond %d)", g, k);
-                    return XD_ESYM;
-                }
-            }
+        int g = 0, k = 0;
+        if (!couplings_invariant(b->N, b->G, b->perms.data(), (const int32_t *)b->bonds.data(), b->nb, J, &g, &k)) {
+            set_error("couplings are not invariant under permutation %d (bond %d)", g, k);
+            return XD_ESYM;
+        }
     }
     h->J.assign(J, J + b->nb);
     XD_CUDA(cudaMemcpy(h->d_J, J, sizeof(double) * b->nb, cudaMemcpyHostToDevice));

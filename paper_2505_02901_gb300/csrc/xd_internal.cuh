@@ -89,6 +89,8 @@ struct SymView {
 struct Bond {
     int i, j;
 };
+// a bond list is read as [nb][2] int32 site pairs (xd_groups.h)
+static_assert(sizeof(Bond) == 2 * sizeof(int32_t), "Bond is two int32 sites");
 
 // Block-structured layout of a large U(1) block (xd_u1_block.cu).
 struct BlockLayoutHost {

@@ -23,6 +23,7 @@
 #include <string>
 #include <unordered_map>
 
+#include "xd_groups.h"
 #include "xd_internal.cuh"
 
 namespace xd {
@@ -755,19 +756,7 @@ xd_status sym_ham_tables(xd_ham_s *h) {
         tab[G + 1 + a] = 1.0 / sqrt((double)a);
     }
     std::vector<int32_t> orb(nb, -1);
-    int norb = 0;
-    for (int q = 0; q < nb; ++q) {
-        if (orb[q] >= 0) continue;
-        for (int g = 0; g < G; ++g) {
-            int a = b->perms[(size_t)g * b->N + b->bonds[q].i];
-            int c = b->perms[(size_t)g * b->N + b->bonds[q].j];
-            for (int p = 0; p < nb; ++p)
-                if (orb[p] < 0 && ((b->bonds[p].i == a && b->bonds[p].j == c) ||
-                                   (b->bonds[p].i == c && b->bonds[p].j == a)))
-                    orb[p] = norb;
-        }
-        ++norb;
-    }
+    bond_orbits(b->N, G, b->perms.data(), (const int32_t *)b->bonds.data(), nb, orb.data());
     memcpy(tab.data() + nsq, orb.data(), nb * sizeof(int32_t));
     XD_CUDA(dev_malloc((void **)&h->d_symtab, tab.size() * sizeof(double)));
     XD_CUDA(cudaMemcpy(h->d_symtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));

@@ -1,0 +1,120 @@
+"""The library's host-side bond-orbit and coupling-invariance helpers
+(csrc/xd_groups.h, plain C++) compiled alone with g++ and checked against a
+brute-force Python reading of the same definitions."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2505_02901_gb300 import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2505_02901_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def shim():
+    out = os.path.join(HERE, "_build")
+    os.makedirs(out, exist_ok=True)
+    so = os.path.join(out, f"libhostgroups.{os.getpid()}.so")
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-I", CSRC, "-o", so,
+                           os.path.join(HERE, "host_groups_shim.cpp")])
+    lib = ctypes.CDLL(so)
+    os.remove(so)
+    P = ctypes.POINTER
+    lib.shim_bond_orbits.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_int32), ctypes.c_int,
+                                     P(ctypes.c_int32)]
+    lib.shim_couplings_invariant.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_int32),
+                                             ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int), P(ctypes.c_int)]
+    return lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def brute_orbits(perms, bonds):
+    """Orbit ids by the definition: bond p joins the orbit of the first bond q
+    whose site pair some g maps onto p's."""
+    pair = [frozenset((int(i), int(j))) for i, j in bonds]
+    orb, n = [-1] * len(bonds), 0
+    for q in range(len(bonds)):
+        if orb[q] >= 0:
+            continue
+        images = {frozenset((int(g[i]), int(g[j]))) for g in perms for i, j in [tuple(bonds[q])]}
+        for p in range(len(bonds)):
+            if orb[p] < 0 and pair[p] in images:
+                orb[p] = n
+        n += 1
+    return orb, n
+
+
+def brute_invariant(perms, bonds, J):
+    pairs = {}
+    for k, (i, j) in enumerate(bonds):
+        pairs.setdefault(frozenset((int(i), int(j))), []).append(k)
+    for g, row in enumerate(perms):
+        for k, (i, j) in enumerate(bonds):
+            hit = pairs.get(frozenset((int(row[i]), int(row[j]))), [])
+            if not any(J[q] == J[k] for q in hit):
+                return 0, g, k
+    return 1, 0, 0
+
+
+CASES = [
+    ("square 4x4 space group, J1-J2", W.space_group(4, 4, "square"), W.square_j1j2(4, 4)[0]),
+    ("triangular 3x3 space group", W.space_group(3, 3, "triangular"), W.triangular(3)[0]),
+    ("6x6 translations, J1-J2", W.torus_translations(6, 6), W.square_j1j2(6, 6)[0]),
+    ("D_12 on the J1-J2 chain", W.chain_dihedral(12), W.chain_j1j2(12)[0]),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_orbits_and_invariance_match_brute_force(shim, case):
+    name, perms, bonds = CASES[case]
+    perms = np.ascontiguousarray(perms, dtype=np.int32)
+    bonds = np.ascontiguousarray(bonds, dtype=np.int32)
+    G, N = perms.shape
+    nb = len(bonds)
+    orb = np.empty(nb, dtype=np.int32)
+    n = shim.shim_bond_orbits(N, G, _p(perms, ctypes.c_int32), _p(bonds, ctypes.c_int32), nb, _p(orb, ctypes.c_int32))
+    ob, nbf = brute_orbits(perms, bonds)
+    assert n == nbf and orb.tolist() == ob, name
+    # couplings constant on each orbit are invariant; breaking one bond is caught
+    rng = np.random.default_rng(case)
+    per_orbit = rng.uniform(0.5, 1.5, n)
+    for J in (per_orbit[orb], np.where(np.arange(nb) == nb // 2, 7.0, per_orbit[orb])):
+        J = np.ascontiguousarray(J, dtype=np.float64)
+        bg, bk = ctypes.c_int(-1), ctypes.c_int(-1)
+        ok = shim.shim_couplings_invariant(N, G, _p(perms, ctypes.c_int32), _p(bonds, ctypes.c_int32), nb,
+                                           _p(J, ctypes.c_double), ctypes.byref(bg), ctypes.byref(bk))
+        want = brute_invariant(perms, bonds, J)
+        assert (ok, bg.value if not ok else 0, bk.value if not ok else 0) == want, name
+
+
+def test_duplicated_bonds(shim):
+    """A ladder that lists every rung twice under its leg translations: the
+    legs are two orbits and all rung copies a third; the two copies of a rung
+    may carry different couplings as long as every rung carries both."""
+    L = 8
+    bonds = np.ascontiguousarray(W.ladder(L, 2), dtype=np.int32)
+    N = 2 * L
+    perms = np.ascontiguousarray([[((i % L + n) % L) + L * (i // L) for i in range(N)] for n in range(L)],
+                                 dtype=np.int32)
+    orb = np.empty(len(bonds), dtype=np.int32)
+    n = shim.shim_bond_orbits(N, L, _p(perms, ctypes.c_int32), _p(bonds, ctypes.c_int32), len(bonds),
+                              _p(orb, ctypes.c_int32))
+    ob, nbf = brute_orbits(perms, bonds)
+    assert n == nbf == 3 and orb.tolist() == ob  # leg 0, leg 1, both rung copies
+    J = np.ones(len(bonds))
+    J[2 * L:3 * L], J[3 * L:] = 0.7, 1.3  # copy A and copy B of every rung
+    J = np.ascontiguousarray(J)
+    bg, bk = ctypes.c_int(), ctypes.c_int()
+    assert shim.shim_couplings_invariant(N, L, _p(perms, ctypes.c_int32), _p(bonds, ctypes.c_int32), len(bonds),
+                                         _p(J, ctypes.c_double), ctypes.byref(bg), ctypes.byref(bk)) == 1
+    J[3 * L] = 0.7  # one rung now has 0.7 twice: the image of copy B (1.3) is missing there
+    assert shim.shim_couplings_invariant(N, L, _p(perms, ctypes.c_int32), _p(bonds, ctypes.c_int32), len(bonds),
+                                         _p(J, ctypes.c_double), ctypes.byref(bg), ctypes.byref(bk)) == 0
+    assert brute_invariant(perms, bonds, J) == (0, bg.value, bk.value)
