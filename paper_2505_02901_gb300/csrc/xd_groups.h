@@ -7,6 +7,7 @@
 
 #include <stdint.h>
 
+#include <string>
 #include <unordered_map>
 #include <vector>
 
@@ -76,6 +77,144 @@ inline int couplings_invariant(int N, int G, const int32_t *perms, const int32_t
         }
     }
     return 1;
+}
+
+// Tables for the orbit search of a symmetric block (Sec. 3.10): the byte
+// tables of the action, and the fast searches that apply to the group.
+//   act[(g nchunk + c) 256 + v] = g applied to the bits v << 8c, where g acts
+//   on a state word by (g s)_i = s_{g(i)}.
+//   Torus: the group holds every translation T_{a,b} of an Lx x Ly torus
+//   (site x + Lx y, 2 <= Lx <= 8).  It is the union of the cosets
+//   {s -> T_{a,b}(p_k s)}, p_0 the identity: tpp[k] = group index of p_k,
+//   tg[k Lx Ly + a + Lx b] = group index of s -> T_{a,b}(p_k s), whose site
+//   map is i -> p_k(T_{a,b}(i)); tnp = number of cosets, 0 when only the
+//   translations; minrot[r] / amask[r] = smallest rotation of an Lx-bit row
+//   and the rotations reaching it; pm[(k - 1) nb + q] = p_k applied to the
+//   mask of bond q (k >= 1).
+//   Ring (only without a torus): the group is the N rotations i -> i + n,
+//   with or without the N reflections i -> n - i (mod N); cg[n] and
+//   cg[N + n] are their group indices, cdih = 1 with reflections.
+struct GroupTables {
+    int nchunk = 0;
+    std::vector<uint64_t> act;
+    int tx = 0, ty = 0, tnp = 0;
+    std::vector<uint8_t> minrot, amask;
+    std::vector<int16_t> tg, tpp;
+    std::vector<uint64_t> pm;
+    int cn = 0, cdih = 0;
+    std::vector<int16_t> cg;
+};
+
+inline void group_tables(int N, int G, const int32_t *perms, const int32_t *bonds, int nb, GroupTables *out) {
+    GroupTables &T = *out;
+    auto perm = [&](int g) { return perms + (size_t)g * N; };
+    T.nchunk = (N + 7) / 8;
+    T.act.assign((size_t)G * T.nchunk * 256, 0);
+    std::vector<int> inv(N);
+    for (int g = 0; g < G; ++g) {
+        for (int i = 0; i < N; ++i) inv[perm(g)[i]] = i;  // bit j of s lands on bit inv[j]
+        for (int c = 0; c < T.nchunk; ++c)
+            for (int val = 0; val < 256; ++val) {
+                uint64_t r = 0;
+                for (int k = 0; k < 8; ++k) {
+                    const int j = 8 * c + k;
+                    if (j < N && ((val >> k) & 1)) r |= 1ull << inv[j];
+                }
+                T.act[((size_t)g * T.nchunk + c) * 256 + val] = r;
+            }
+    }
+    std::unordered_map<std::string, int> index;  // permutation -> group index
+    auto key = [&](const int32_t *q) { return std::string((const char *)q, sizeof(int32_t) * N); };
+    for (int g = 0; g < G; ++g) index.emplace(key(perm(g)), g);
+    for (int Lx = 2; Lx <= 8 && !T.tx; ++Lx) {
+        if (N % Lx || G % N) continue;
+        const int Ly = N / Lx, nt = N;
+        std::vector<int32_t> q(N);
+        std::vector<int> tr(nt, -1);  // group index of T_{a,b}, at a + Lx b
+        bool ok = true;
+        for (int t = 0; t < nt && ok; ++t) {
+            const int a = t % Lx, bb = t / Lx;
+            for (int i = 0; i < N; ++i) q[i] = ((i % Lx + a) % Lx) + Lx * ((i / Lx + bb) % Ly);
+            auto it = index.find(key(q.data()));
+            if (it == index.end()) ok = false;
+            else tr[t] = it->second;
+        }
+        if (!ok) continue;
+        // the identity (tr[0]) first, so that p_0 is the identity
+        std::vector<int16_t> tg, tpp;
+        std::vector<char> covered(G, 0);
+        for (int n = -1; n < G && ok; ++n) {
+            const int g = n < 0 ? tr[0] : n;
+            if (covered[g]) continue;
+            tpp.push_back((int16_t)g);
+            for (int t = 0; t < nt && ok; ++t) {
+                const int32_t *pt = perm(tr[t]);
+                for (int i = 0; i < N; ++i) q[i] = perm(g)[pt[i]];
+                auto it = index.find(key(q.data()));
+                if (it == index.end() || covered[it->second]) {
+                    ok = false;
+                } else {
+                    covered[it->second] = 1;
+                    tg.push_back((int16_t)it->second);
+                }
+            }
+        }
+        if (!ok || (int)tpp.size() * nt != G) continue;
+        T.minrot.assign(1u << Lx, 0);
+        T.amask.assign(1u << Lx, 0);
+        for (uint32_t r = 0; r < (1u << Lx); ++r) {
+            uint32_t m = r, mask = 0;
+            for (int a = 0; a < Lx; ++a) {
+                const uint32_t rr = ((r >> a) | (r << (Lx - a))) & ((1u << Lx) - 1);
+                if (rr < m) {
+                    m = rr;
+                    mask = 1u << a;
+                } else if (rr == m) {
+                    mask |= 1u << a;
+                }
+            }
+            T.minrot[r] = (uint8_t)m;
+            T.amask[r] = (uint8_t)mask;
+        }
+        T.tx = Lx;
+        T.ty = Ly;
+        T.tnp = tpp.size() > 1 ? (int)tpp.size() : 0;
+        T.tg = tg;
+        T.tpp = tpp;
+        T.pm.assign((size_t)(T.tnp > 1 ? T.tnp - 1 : 0) * nb, 0);
+        for (int k = 1; k < T.tnp; ++k) {
+            for (int i = 0; i < N; ++i) inv[perm(tpp[k])[i]] = i;
+            for (int b = 0; b < nb; ++b)
+                T.pm[(size_t)(k - 1) * nb + b] = (1ull << inv[bonds[2 * b]]) | (1ull << inv[bonds[2 * b + 1]]);
+        }
+    }
+    if (!T.tx && N <= 64 && (G == N || G == 2 * N)) {
+        std::vector<int16_t> cg(2 * N, -1);
+        bool ok = true;
+        for (int g = 0; g < G && ok; ++g) {
+            const int32_t *p = perm(g);
+            const int n = p[0];
+            bool rot = true, ref = true;
+            for (int i = 0; i < N; ++i) {
+                rot = rot && p[i] == (i + n) % N;
+                ref = ref && p[i] == ((n - i) % N + N) % N;
+            }
+            if (N > 2 && rot && ref) ok = false;  // only the identity of N <= 2 is both
+            const int slot = rot ? n : ref ? N + n : -1;
+            if (slot < 0 || cg[slot] >= 0) ok = false;
+            else cg[slot] = (int16_t)g;
+        }
+        int nrot = 0, nref = 0;
+        for (int n = 0; n < N; ++n) {
+            nrot += cg[n] >= 0;
+            nref += cg[N + n] >= 0;
+        }
+        if (ok && nrot == N && (nref == 0 || nref == N) && N + nref == G) {
+            T.cn = N;
+            T.cdih = nref ? 1 : 0;
+            T.cg = cg;
+        }
+    }
 }
 
 }  // namespace xd

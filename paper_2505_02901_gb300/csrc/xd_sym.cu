@@ -552,143 +552,39 @@ __global__ void k_orbit_mean(const double *__restrict__ part, int rows, int nb,
 
 }  // namespace
 
+template <typename E>
+static xd_status upload(E **dst, const std::vector<E> &v) {
+    XD_CUDA(dev_malloc((void **)dst, std::max<size_t>(1, v.size()) * sizeof(E)));
+    XD_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(E), cudaMemcpyHostToDevice));
+    return XD_OK;
+}
+
 static xd_status make_tables(xd_basis_s *b) {
     const int N = b->N, G = b->G;
-    b->nchunk = (N + 7) / 8;
-    std::vector<uint64_t> tab((size_t)G * b->nchunk * 256, 0);
-    for (int g = 0; g < G; ++g) {
-        const int32_t *p = b->perms.data() + (size_t)g * N;
-        std::vector<int> inv(N);
-        for (int i = 0; i < N; ++i) inv[p[i]] = i;  // bit j of s lands on bit inv[j]
-        for (int c = 0; c < b->nchunk; ++c)
-            for (int val = 0; val < 256; ++val) {
-                uint64_t r = 0;
-                for (int k = 0; k < 8; ++k) {
-                    int j = 8 * c + k;
-                    if (j < N && ((val >> k) & 1)) r |= 1ull << inv[j];
-                }
-                tab[((size_t)g * b->nchunk + c) * 256 + val] = r;
-            }
+    GroupTables T;
+    group_tables(N, G, b->perms.data(), (const int32_t *)b->bonds.data(), b->nb, &T);
+    b->nchunk = T.nchunk;
+    if (T.tx) {
+        XD_TRY(upload(&b->d_minrot, T.minrot));
+        XD_TRY(upload(&b->d_amask, T.amask));
+        XD_TRY(upload(&b->d_tg, T.tg));
+        XD_TRY(upload(&b->d_tpp, T.tpp));
+        if (T.tnp) XD_TRY(upload(&b->d_pm, T.pm));
+        b->tx = T.tx;
+        b->ty = T.ty;
+        b->tnp = T.tnp;
+    } else if (T.cn) {
+        XD_TRY(upload(&b->d_cg, T.cg));
+        b->cn = T.cn;
+        b->cdih = T.cdih;
     }
-    // translation group of an Lx x Ly torus (rows of at most 8 sites) inside
-    // the group, and its cosets T p_k?
-    std::unordered_map<std::string, int> index;  // permutation -> group index
-    auto perm = [&](int g) { return b->perms.data() + (size_t)g * N; };
-    auto key = [&](const int32_t *q) { return std::string((const char *)q, sizeof(int32_t) * N); };
-    for (int g = 0; g < G; ++g) index.emplace(key(perm(g)), g);
-    for (int Lx = 2; Lx <= 8 && !b->tx; ++Lx) {
-        if (N % Lx || G % N) continue;
-        const int Ly = N / Lx, T = N;
-        std::vector<int32_t> q(N);
-        std::vector<int> tr(T, -1);  // group index of T_{a,b}, at a + Lx b
-        bool ok = true;
-        for (int t = 0; t < T && ok; ++t) {
-            const int a = t % Lx, bb = t / Lx;
-            for (int i = 0; i < N; ++i) q[i] = ((i % Lx + a) % Lx) + Lx * ((i / Lx + bb) % Ly);
-            auto it = index.find(key(q.data()));
-            if (it == index.end()) ok = false;
-            else tr[t] = it->second;
-        }
-        if (!ok) continue;
-        // cosets: s -> T_{a,b}(p s) has the site map i -> p[T_{a,b}[i]]; the
-        // identity (tr[0]) is taken first so that p_0 is the identity
-        std::vector<int16_t> tg, tpp;
-        std::vector<char> covered(G, 0);
-        for (int n = -1; n < G && ok; ++n) {
-            const int g = n < 0 ? tr[0] : n;
-            if (covered[g]) continue;
-            tpp.push_back((int16_t)g);
-            for (int t = 0; t < T && ok; ++t) {
-                const int32_t *pt = perm(tr[t]);
-                for (int i = 0; i < N; ++i) q[i] = perm(g)[pt[i]];
-                auto it = index.find(key(q.data()));
-                if (it == index.end() || covered[it->second]) {
-                    ok = false;
-                } else {
-                    covered[it->second] = 1;
-                    tg.push_back((int16_t)it->second);
-                }
-            }
-        }
-        if (!ok || (int)tpp.size() * T != G) continue;
-        std::vector<uint8_t> minrot(1u << Lx), amask(1u << Lx);
-        for (uint32_t r = 0; r < (1u << Lx); ++r) {
-            uint32_t m = r, mask = 0;
-            for (int a = 0; a < Lx; ++a) {
-                const uint32_t rr = ((r >> a) | (r << (Lx - a))) & ((1u << Lx) - 1);
-                if (rr < m) {
-                    m = rr;
-                    mask = 1u << a;
-                } else if (rr == m) {
-                    mask |= 1u << a;
-                }
-            }
-            minrot[r] = (uint8_t)m;
-            amask[r] = (uint8_t)mask;
-        }
-        XD_CUDA(dev_malloc((void **)&b->d_minrot, minrot.size()));
-        XD_CUDA(dev_malloc((void **)&b->d_amask, amask.size()));
-        XD_CUDA(dev_malloc((void **)&b->d_tg, tg.size() * sizeof(int16_t)));
-        XD_CUDA(dev_malloc((void **)&b->d_tpp, tpp.size() * sizeof(int16_t)));
-        XD_CUDA(cudaMemcpy(b->d_minrot, minrot.data(), minrot.size(), cudaMemcpyHostToDevice));
-        XD_CUDA(cudaMemcpy(b->d_amask, amask.data(), amask.size(), cudaMemcpyHostToDevice));
-        XD_CUDA(cudaMemcpy(b->d_tg, tg.data(), tg.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
-        XD_CUDA(cudaMemcpy(b->d_tpp, tpp.data(), tpp.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
-        b->tx = Lx;
-        b->ty = Ly;
-        b->tnp = tpp.size() > 1 ? (int)tpp.size() : 0;
-        if (b->tnp) {
-            const int nb = b->nb;
-            std::vector<uint64_t> pm((size_t)(b->tnp - 1) * nb);
-            std::vector<int> inv(N);
-            for (int k = 1; k < b->tnp; ++k) {
-                const int32_t *p = perm(tpp[k]);
-                for (int i = 0; i < N; ++i) inv[p[i]] = i;  // bit j of s lands on bit inv[j]
-                for (int q = 0; q < nb; ++q)
-                    pm[(size_t)(k - 1) * nb + q] = (1ull << inv[b->bonds[q].i]) | (1ull << inv[b->bonds[q].j]);
-            }
-            XD_CUDA(dev_malloc((void **)&b->d_pm, pm.size() * sizeof(uint64_t)));
-            XD_CUDA(cudaMemcpy(b->d_pm, pm.data(), pm.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
-        }
-    }
-    // rotations of a ring, with or without its reflections?
-    if (!b->tx && N <= 64 && (G == N || G == 2 * N)) {
-        std::vector<int16_t> cg(2 * N, -1);
-        bool ok = true;
-        for (int g = 0; g < G && ok; ++g) {
-            const int32_t *p = b->perms.data() + (size_t)g * N;
-            const int n = p[0];
-            bool rot = true, ref = true;
-            for (int i = 0; i < N; ++i) {
-                rot = rot && p[i] == (i + n) % N;
-                ref = ref && p[i] == ((n - i) % N + N) % N;
-            }
-            if (N > 2 && rot && ref) ok = false;  // only the identity of N <= 2 is both
-            const int slot = rot ? n : ref ? N + n : -1;
-            if (slot < 0 || cg[slot] >= 0) ok = false;
-            else cg[slot] = (int16_t)g;
-        }
-        int nrot = 0, nref = 0;
-        for (int n = 0; n < N; ++n) {
-            nrot += cg[n] >= 0;
-            nref += cg[N + n] >= 0;
-        }
-        if (ok && nrot == N && (nref == 0 || nref == N) && N + nref == G) {
-            XD_CUDA(dev_malloc((void **)&b->d_cg, cg.size() * sizeof(int16_t)));
-            XD_CUDA(cudaMemcpy(b->d_cg, cg.data(), cg.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
-            b->cn = N;
-            b->cdih = nref ? 1 : 0;
-        }
-    }
-    XD_CUDA(dev_malloc((void **)&b->d_act, tab.size() * sizeof(uint64_t)));
-    XD_CUDA(cudaMemcpy(b->d_act, tab.data(), tab.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
+    XD_TRY(upload(&b->d_act, T.act));
     std::vector<double> chi(2 * G);
     for (int g = 0; g < G; ++g) {
         chi[2 * g] = b->chi_re[g];
         chi[2 * g + 1] = b->chi_im[g];
     }
-    XD_CUDA(dev_malloc((void **)&b->d_chi, chi.size() * sizeof(double)));
-    XD_CUDA(cudaMemcpy(b->d_chi, chi.data(), chi.size() * sizeof(double), cudaMemcpyHostToDevice));
+    XD_TRY(upload(&b->d_chi, chi));
     return XD_OK;
 }
 

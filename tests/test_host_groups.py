@@ -118,3 +118,88 @@ def test_duplicated_bonds(shim):
     assert shim.shim_couplings_invariant(N, L, _p(perms, ctypes.c_int32), _p(bonds, ctypes.c_int32), len(bonds),
                                          _p(J, ctypes.c_double), ctypes.byref(bg), ctypes.byref(bk)) == 0
     assert brute_invariant(perms, bonds, J) == (0, bg.value, bk.value)
+
+
+def _act(perm, s):
+    """(g s)_i = s_{g(i)} on a state word."""
+    return sum(((s >> int(perm[i])) & 1) << i for i in range(len(perm)))
+
+
+def _tables(shim, perms, bonds):
+    perms = np.ascontiguousarray(perms, dtype=np.int32)
+    bonds = np.ascontiguousarray(bonds, dtype=np.int32)
+    G, N = perms.shape
+    nb = len(bonds)
+    nchunk = (N + 7) // 8
+    meta = np.zeros(6, dtype=np.int32)
+    act = np.zeros(G * nchunk * 256, dtype=np.uint64)
+    minrot, amask = np.zeros(256, dtype=np.uint8), np.zeros(256, dtype=np.uint8)
+    tg, tpp = np.full(G, -1, dtype=np.int16), np.full(G, -1, dtype=np.int16)
+    pm = np.zeros(max(1, G * nb), dtype=np.uint64)
+    cg = np.full(2 * N, -1, dtype=np.int16)
+    P = ctypes.POINTER
+    shim.shim_group_tables.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_int32), ctypes.c_int,
+                                       P(ctypes.c_int32), P(ctypes.c_uint64), P(ctypes.c_uint8), P(ctypes.c_uint8),
+                                       P(ctypes.c_int16), P(ctypes.c_int16), P(ctypes.c_uint64), P(ctypes.c_int16)]
+    shim.shim_group_tables(N, G, _p(perms, ctypes.c_int32), _p(bonds, ctypes.c_int32), nb, _p(meta, ctypes.c_int32),
+                           _p(act, ctypes.c_uint64), _p(minrot, ctypes.c_uint8), _p(amask, ctypes.c_uint8),
+                           _p(tg, ctypes.c_int16), _p(tpp, ctypes.c_int16), _p(pm, ctypes.c_uint64),
+                           _p(cg, ctypes.c_int16))
+    return perms, bonds, dict(zip(("nchunk", "tx", "ty", "tnp", "cn", "cdih"), meta.tolist())), act, minrot, amask, \
+        tg, tpp, pm, cg
+
+
+GROUPS = [
+    # name, perms, bonds, expected (tx, ty, cosets or 0, ring cn, cdih)
+    ("square 4x4 space group", W.space_group(4, 4, "square"), W.square_j1j2(4, 4)[0], (4, 4, 8, 0, 0)),
+    ("triangular 3x3 space group", W.space_group(3, 3, "triangular"), W.triangular(3)[0], (3, 3, 12, 0, 0)),
+    ("rectangular 4x6 space group", W.space_group(4, 6, "rectangular"), W.square_j1j2(4, 6)[0], (4, 6, 4, 0, 0)),
+    ("6x6 translations", W.torus_translations(6, 6), W.square_j1j2(6, 6)[0], (6, 6, 0, 0, 0)),
+    ("D_8 (one-row torus)", W.chain_dihedral(8), W.chain(8), (8, 1, 2, 0, 0)),
+    ("D_12 (ring)", W.chain_dihedral(12), W.chain_j1j2(12)[0], (0, 0, 0, 12, 1)),
+    ("C_12 (ring)", W.chain_translations(12), W.chain(12), (0, 0, 0, 12, 0)),
+    ("C4v alone on 4x4 (no translations)", W.space_group(4, 4, "square")[::16], W.square_j1j2(4, 4)[0],
+     (0, 0, 0, 0, 0)),
+]
+
+
+@pytest.mark.parametrize("case", range(len(GROUPS)))
+def test_group_tables(shim, case):
+    name, perms, bonds, want = GROUPS[case]
+    rng = np.random.default_rng(case)
+    perms = np.asarray(perms)
+    scramble = rng.permutation(len(perms))  # any element order
+    scramble = np.r_[scramble[scramble == 0], scramble[scramble != 0]] if case % 2 else scramble
+    perms, bonds, m, act, minrot, amask, tg, tpp, pm, cg = _tables(shim, perms[scramble], bonds)
+    G, N = perms.shape
+    assert (m["tx"], m["ty"], m["tnp"], m["cn"], m["cdih"]) == want, name
+    # byte tables of the action
+    for _ in range(20):
+        s = int(rng.integers(0, 1 << N))
+        for g in rng.integers(0, G, 3):
+            got = 0
+            for c in range(m["nchunk"]):
+                got |= int(act[(int(g) * m["nchunk"] + c) * 256 + ((s >> (8 * c)) & 255)])
+            assert got == _act(perms[g], s)
+    if m["tx"]:
+        Lx, Ly = m["tx"], m["ty"]
+        ncos = max(1, m["tnp"])
+        assert (perms[tpp[0]] == np.arange(N)).all()  # p_0 is the identity
+        assert sorted(tg[:ncos * N].tolist()) == list(range(G))  # every element once
+        for k in range(ncos):
+            for t in range(N):
+                a, b = t % Lx, t // Lx
+                tr = [((i % Lx + a) % Lx) + Lx * ((i // Lx + b) % Ly) for i in range(N)]
+                assert perms[tg[k * N + t]].tolist() == [int(perms[tpp[k]][tr[i]]) for i in range(N)]
+        for r in range(1 << Lx):
+            rots = [((r >> a) | (r << (Lx - a))) & ((1 << Lx) - 1) for a in range(Lx)]
+            assert minrot[r] == min(rots)
+            assert amask[r] == sum(1 << a for a in range(Lx) if rots[a] == min(rots))
+        for k in range(1, m["tnp"]):
+            for q, (i, j) in enumerate(bonds):
+                assert int(pm[(k - 1) * len(bonds) + q]) == _act(perms[tpp[k]], (1 << int(i)) | (1 << int(j)))
+    if m["cn"]:
+        for n in range(N):
+            assert perms[cg[n]].tolist() == [(i + n) % N for i in range(N)]
+            if m["cdih"]:
+                assert perms[cg[N + n]].tolist() == [(n - i) % N for i in range(N)]
