@@ -17,6 +17,7 @@
 #include <unordered_map>
 
 #include "xd_groups.h"
+#include "xd_layout.h"
 #include "xd_internal.cuh"
 
 namespace xd {
@@ -90,44 +91,19 @@ xd_status ensure_partials(xd_ham_s *h, size_t bytes) {
     return XD_OK;
 }
 
-// Choose the postfix width L.  Blocks hold C(L, m) rows, so L bounds the
-// block size; the prefix table has 2^(N-L) entries.
-static int choose_L(int N) {
-    if (N <= 8) return N;
-    int L = (N + 1) / 2;
-    if (L > 16) L = 16;
-    if (N - L > 24) L = N - 24;
-    return L;
-}
-
 static xd_status build_u1(xd_basis_s *b) {
-    const int N = b->N, nup = b->nup;
-    const int L = choose_L(N), P = N - L;
-    b->L = L;
-    b->P = P;
-    const uint64_t nlo = 1ull << L, nhi = 1ull << P;
-    b->h_lo_off.assign(L + 2, 0);
-    for (int m = 0; m <= L; ++m) b->h_lo_off[m + 1] = b->h_lo_off[m] + (uint32_t)binom(L, m);
-    b->h_lo_rank.assign(nlo, 0);
-    b->h_lo_list.assign(nlo, 0);
-    std::vector<uint32_t> fill(b->h_lo_off.begin(), b->h_lo_off.end() - 1);
-    for (uint64_t l = 0; l < nlo; ++l) {  // ascending l: ranks in class order
-        int m = popc64(l);
-        uint32_t r = fill[m]++ - b->h_lo_off[m];
-        b->h_lo_rank[l] = r;
-        b->h_lo_list[b->h_lo_off[m] + r] = (uint32_t)l;
-    }
-    b->h_hi_off.assign(nhi + 1, 0);
-    for (uint64_t h = 0; h < nhi; ++h) {
-        int m = nup - popc64(h);
-        int64_t sz = (m >= 0 && m <= L) ? binom(L, m) : 0;
-        b->h_hi_off[h + 1] = b->h_hi_off[h] + sz;
-    }
-    b->dim_u1 = b->h_hi_off[nhi];
-    if (b->dim_u1 != binom(N, nup)) {
-        set_error("internal: U(1) layout size %lld != C(%d,%d)", (long long)b->dim_u1, N, nup);
+    U1Layout lay;
+    if (!u1_layout(b->N, b->nup, &lay)) {
+        set_error("internal: U(1) layout size %lld != C(%d,%d)", (long long)lay.dim, b->N, b->nup);
         return XD_ERANGE;
     }
+    b->L = lay.L;
+    b->P = lay.P;
+    b->dim_u1 = lay.dim;
+    b->h_hi_off = std::move(lay.hi_off);
+    b->h_lo_rank = std::move(lay.lo_rank);
+    b->h_lo_list = std::move(lay.lo_list);
+    b->h_lo_off = std::move(lay.lo_off);
     XD_TRY(dcopy(&b->d_hi_off, b->h_hi_off.data(), b->h_hi_off.size()));
     XD_TRY(dcopy(&b->d_lo_rank, b->h_lo_rank.data(), b->h_lo_rank.size()));
     XD_TRY(dcopy(&b->d_lo_list, b->h_lo_list.data(), b->h_lo_list.size()));
@@ -136,19 +112,11 @@ static xd_status build_u1(xd_basis_s *b) {
 }
 
 static int64_t u1_index_host(const xd_basis_s *b, uint64_t s) {
-    if (b->N < 64 && (s >> b->N)) return -1;
-    if (popc64(s) != b->nup) return -1;
-    uint64_t lomask = (1ull << b->L) - 1;
-    return b->h_hi_off[s >> b->L] + b->h_lo_rank[s & lomask];
+    return u1_index(b->N, b->nup, b->L, b->h_hi_off, b->h_lo_rank, s);
 }
 
 static uint64_t u1_state_host(const xd_basis_s *b, int64_t idx) {
-    // block: last h with hi_off[h] <= idx
-    auto it = std::upper_bound(b->h_hi_off.begin(), b->h_hi_off.end(), idx);
-    uint64_t h = (uint64_t)(it - b->h_hi_off.begin()) - 1;
-    int m = b->nup - popc64(h);
-    uint32_t l = b->h_lo_list[b->h_lo_off[m] + (uint32_t)(idx - b->h_hi_off[h])];
-    return (h << b->L) | l;
+    return u1_state(b->nup, b->L, b->h_hi_off, b->h_lo_list, b->h_lo_off, idx);
 }
 
 // Group axioms and homomorphism (Sec. 3.9.1, Sec. 3.9.2), invariance of the
