@@ -86,4 +86,71 @@ inline uint64_t u1_state(int nup, int L, const std::vector<int64_t> &hi_off, con
     return (h << L) | l;
 }
 
+// Tables of the block-structured product (one CTA per prefix block).  Bonds
+// are postfix (both sites < L), prefix (both >= L: the pair of prefix bits,
+// as (a, b, bond) triples) or cross (one site each side: (prefix bit,
+// postfix site, bond, slot) quadruples, grouped by prefix bit; csite =
+// (prefix bit, first, end) per group; slot = index of the postfix site among
+// the distinct cross postfix sites).  Tables are indexed by the class-ordered
+// position g of the postfix word l = lo_list[g]:
+//   ptab[q 2^L + g] = rank of l with postfix bond q flipped, or maxblk ("no
+//   flip" and padding rows; the kernel keeps a zero there),
+//   xtab[slot 2^L + g] = rank of l with the slot's postfix site flipped.
+struct BlockTables {
+    std::vector<int32_t> post, pre, cross, csite;
+    std::vector<int> slot_site;
+    std::vector<uint16_t> ptab, xtab;
+    std::vector<uint32_t> order;  // prefixes with a non-empty block, ascending
+    int npost_pad = 0, maxblk = 0;
+};
+
+inline void block_tables(int N, int nup, int L, const int32_t *bonds, int nb, const std::vector<uint32_t> &lo_rank,
+                         const std::vector<uint32_t> &lo_list, BlockTables *out) {
+    BlockTables &B = *out;
+    const int P = N - L;
+    for (int k = 0; k < nb; ++k) {
+        int i = bonds[2 * k], j = bonds[2 * k + 1];
+        if (i > j) std::swap(i, j);
+        if (j < L) {
+            B.post.push_back(k);
+        } else if (i >= L) {
+            B.pre.insert(B.pre.end(), {i - L, j - L, k});
+        } else {
+            int slot = (int)(std::find(B.slot_site.begin(), B.slot_site.end(), i) - B.slot_site.begin());
+            if (slot == (int)B.slot_site.size()) B.slot_site.push_back(i);
+            B.cross.insert(B.cross.end(), {j - L, i, k, slot});
+        }
+    }
+    const int nc = (int)B.cross.size() / 4;
+    std::vector<int> idx(nc);
+    for (int q = 0; q < nc; ++q) idx[q] = q;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return B.cross[4 * a] < B.cross[4 * c]; });
+    std::vector<int32_t> sorted;
+    for (int q : idx) sorted.insert(sorted.end(), B.cross.begin() + 4 * q, B.cross.begin() + 4 * q + 4);
+    B.cross.swap(sorted);
+    for (int q = 0; q < nc; ++q)
+        if (q == 0 || B.cross[4 * q] != B.cross[4 * (q - 1)]) B.csite.insert(B.csite.end(), {B.cross[4 * q], q, q + 1});
+        else B.csite.back() = q + 1;
+    const int npost = (int)B.post.size();
+    B.npost_pad = (npost + 7) / 8 * 8;
+    B.maxblk = (int)n_choose_k(L, L / 2);
+    const uint32_t nlo = 1u << L;
+    const uint16_t noflip = (uint16_t)B.maxblk;
+    B.ptab.assign((size_t)B.npost_pad * nlo, noflip);
+    B.xtab.assign(B.slot_site.size() * nlo, 0);
+    for (uint32_t g = 0; g < nlo; ++g) {
+        const uint32_t l = lo_list[g];
+        for (int q = 0; q < npost; ++q) {
+            const int i = bonds[2 * B.post[q]], j = bonds[2 * B.post[q] + 1];
+            if (((l >> i) & 1) != ((l >> j) & 1)) B.ptab[(size_t)q * nlo + g] = (uint16_t)lo_rank[l ^ (1u << i) ^ (1u << j)];
+        }
+        for (size_t q = 0; q < B.slot_site.size(); ++q)
+            B.xtab[q * nlo + g] = (uint16_t)lo_rank[l ^ (1u << B.slot_site[q])];
+    }
+    for (uint64_t h = 0; h < (1ull << P); ++h) {
+        const int m = nup - __builtin_popcountll(h);
+        if (m >= 0 && m <= L) B.order.push_back((uint32_t)h);
+    }
+}
+
 }  // namespace xd

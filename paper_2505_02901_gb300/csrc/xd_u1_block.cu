@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "xd_internal.cuh"
+#include "xd_layout.h"
 
 namespace xd {
 
@@ -302,13 +303,6 @@ __global__ void __launch_bounds__(kBT) k_block_apply(BlkParams p, const T *__res
 
 // ------------------------------------------------------------ host side
 
-static int64_t binom_h(int n, int k) {
-    if (k < 0 || k > n) return 0;
-    int64_t r = 1;
-    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
-    return r;
-}
-
 bool block_layout_wanted(const xd_basis_s *b) {
     if (b->sym || b->N < 20 || b->L < 10) return false;
     int ncross = 0;
@@ -320,68 +314,21 @@ bool block_layout_wanted(const xd_basis_s *b) {
 }
 
 xd_status block_layout_build(xd_basis_s *b) {
-    const int L = b->L, P = b->P, nup = b->nup;
+    const int L = b->L, nup = b->nup;
     BlockLayoutHost &bl = b->blk;
-    // classify bonds
-    std::vector<int32_t> pre, cross, post;
-    std::vector<int> slot_site;
-    for (int k = 0; k < b->nb; ++k) {
-        int i = b->bonds[k].i, j = b->bonds[k].j;
-        if (i > j) std::swap(i, j);
-        if (j < L) {
-            post.push_back(k);
-        } else if (i >= L) {
-            pre.insert(pre.end(), {i - L, j - L, k});
-        } else {
-            int slot = (int)(std::find(slot_site.begin(), slot_site.end(), i) - slot_site.begin());
-            if (slot == (int)slot_site.size()) slot_site.push_back(i);
-            cross.insert(cross.end(), {j - L, i, k, slot});
-        }
-    }
-    // cross bonds grouped by prefix site: csite = (prefix bit, first, end)
-    std::vector<int32_t> csite;
-    {
-        const int nc = (int)cross.size() / 4;
-        std::vector<int> idx(nc);
-        for (int q = 0; q < nc; ++q) idx[q] = q;
-        std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return cross[4 * a] < cross[4 * c]; });
-        std::vector<int32_t> sorted;
-        for (int q : idx) sorted.insert(sorted.end(), cross.begin() + 4 * q, cross.begin() + 4 * q + 4);
-        cross.swap(sorted);
-        for (int q = 0; q < nc; ++q)
-            if (q == 0 || cross[4 * q] != cross[4 * (q - 1)]) csite.insert(csite.end(), {cross[4 * q], q, q + 1});
-            else csite.back() = q + 1;
-    }
-    bl.ncsite = (int)csite.size() / 3;
-    bl.npre = (int)pre.size() / 3;
-    bl.ncross = (int)cross.size() / 4;
-    bl.npost = (int)post.size();
-    bl.npost_pad = (bl.npost + 7) / 8 * 8;
-    bl.post.assign(post.begin(), post.end());
-    // target tables indexed by the class-ordered position g of the postfix word;
-    // "no flip" and padding entries point at the kernel's zero slot
-    const uint32_t nlo = 1u << L;
-    const uint16_t noflip = (uint16_t)binom_h(L, L / 2);  // the kernel's zero slot
-    std::vector<uint16_t> ptab((size_t)bl.npost_pad * nlo, noflip), xtab((size_t)slot_site.size() * nlo);
-    for (uint32_t g = 0; g < nlo; ++g) {
-        const uint32_t l = b->h_lo_list[g];
-        for (int q = 0; q < bl.npost; ++q) {
-            int i = b->bonds[post[q]].i, j = b->bonds[post[q]].j;
-            uint16_t v = noflip;
-            if (((l >> i) & 1) != ((l >> j) & 1)) v = (uint16_t)b->h_lo_rank[l ^ (1u << i) ^ (1u << j)];
-            ptab[(size_t)q * nlo + g] = v;
-        }
-        for (size_t q = 0; q < slot_site.size(); ++q)
-            xtab[q * nlo + g] = (uint16_t)b->h_lo_rank[l ^ (1u << slot_site[q])];
-    }
-    // non-empty prefix blocks in ascending order
-    std::vector<uint32_t> order;
-    for (uint64_t h = 0; h < (1ull << P); ++h) {
-        int m = nup - __builtin_popcountll(h);
-        if (m >= 0 && m <= L) order.push_back((uint32_t)h);
-    }
-    bl.nblk = (int64_t)order.size();
-    bl.maxblk = (int)binom_h(L, L / 2);
+    BlockTables T;
+    block_tables(b->N, nup, L, (const int32_t *)b->bonds.data(), b->nb, b->h_lo_rank, b->h_lo_list, &T);
+    bl.ncsite = (int)T.csite.size() / 3;
+    bl.npre = (int)T.pre.size() / 3;
+    bl.ncross = (int)T.cross.size() / 4;
+    bl.npost = (int)T.post.size();
+    bl.npost_pad = T.npost_pad;
+    bl.post.assign(T.post.begin(), T.post.end());
+    bl.nblk = (int64_t)T.order.size();
+    bl.maxblk = T.maxblk;
+    const std::vector<uint32_t> &order = T.order;
+    const std::vector<int32_t> &post = T.post, &pre = T.pre, &cross = T.cross, &csite = T.csite;
+    const std::vector<uint16_t> &ptab = T.ptab, &xtab = T.xtab;
     auto up = [](auto **dst, const auto &v) -> xd_status {
         using E = typename std::remove_reference<decltype(v)>::type::value_type;
         XD_CUDA(dev_malloc((void **)dst, std::max<size_t>(1, v.size()) * sizeof(E)));

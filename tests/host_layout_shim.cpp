@@ -20,3 +20,29 @@ extern "C" long long shim_u1_index(unsigned long long s) {
 extern "C" unsigned long long shim_u1_state(long long idx) {
     return xd::u1_state(g_nup, g_lay.L, g_lay.hi_off, g_lay.lo_list, g_lay.lo_off, idx);
 }
+
+static xd::BlockTables g_blk;
+
+// sizes: L, npost, npre, ncross, ncsite, nslot, npost_pad, maxblk, norder
+extern "C" void shim_block_build(int N, int nup, const int32_t *bonds, int nb, int *sizes) {
+    g_N = N;
+    g_nup = nup;
+    xd::u1_layout(N, nup, &g_lay);
+    g_blk = xd::BlockTables();
+    xd::block_tables(N, nup, g_lay.L, bonds, nb, g_lay.lo_rank, g_lay.lo_list, &g_blk);
+    const int s[9] = {g_lay.L, (int)g_blk.post.size(), (int)g_blk.pre.size() / 3, (int)g_blk.cross.size() / 4,
+                      (int)g_blk.csite.size() / 3, (int)g_blk.slot_site.size(), g_blk.npost_pad, g_blk.maxblk,
+                      (int)g_blk.order.size()};
+    for (int i = 0; i < 9; ++i) sizes[i] = s[i];
+}
+extern "C" const int64_t *shim_hi_off() { return g_lay.hi_off.data(); }
+extern "C" const uint32_t *shim_lo_rank() { return g_lay.lo_rank.data(); }
+extern "C" const uint32_t *shim_lo_list() { return g_lay.lo_list.data(); }
+extern "C" const uint32_t *shim_lo_off() { return g_lay.lo_off.data(); }
+extern "C" const int32_t *shim_post() { return g_blk.post.data(); }
+extern "C" const int32_t *shim_pre() { return g_blk.pre.data(); }
+extern "C" const int32_t *shim_cross() { return g_blk.cross.data(); }
+extern "C" const int32_t *shim_csite() { return g_blk.csite.data(); }
+extern "C" const uint16_t *shim_ptab() { return g_blk.ptab.data(); }
+extern "C" const uint16_t *shim_xtab() { return g_blk.xtab.data(); }
+extern "C" const uint32_t *shim_order() { return g_blk.order.data(); }

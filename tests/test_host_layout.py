@@ -63,3 +63,89 @@ def test_sampled_words_large_blocks(lay, orc, N, nup, L):
         s = orc.state_count(N, nup, int(idx))
         assert lay.shim_u1_state(int(idx)) == s
         assert lay.shim_u1_index(s) == int(idx) == orc.index_count(N, nup, s)
+
+
+def _arr(fn, ctype, n):
+    fn.restype = ctypes.POINTER(ctype)
+    return np.ctypeslib.as_array(fn(), shape=(max(1, n),))[:n].copy() if n else np.zeros(0)
+
+
+def block_product_twin(lay, N, nup, bonds, J, x):
+    """y = H x read off the block tables the way the FP64 block kernel uses
+    them: per prefix block h, postfix flips through ptab (the zero slot for
+    "no flip"), prefix flips as whole neighbour blocks at the same position,
+    cross flips through xtab from the neighbour block of the flipped prefix
+    bit with J/2 (x_target - x_row), and the diagonal J_cross/4 + prefix
+    and postfix terms."""
+    bonds = np.ascontiguousarray(bonds, dtype=np.int32)
+    sz = (ctypes.c_int * 9)()
+    lay.shim_block_build(N, nup, bonds.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(bonds), sz)
+    L, npost, npre, ncross, ncsite, nslot, npost_pad, maxblk, norder = list(sz)
+    P, nlo = N - L, 1 << L
+    hi_off = _arr(lay.shim_hi_off, ctypes.c_int64, (1 << P) + 1)
+    lo_list = _arr(lay.shim_lo_list, ctypes.c_uint32, nlo)
+    lo_off = _arr(lay.shim_lo_off, ctypes.c_uint32, L + 2)
+    post = _arr(lay.shim_post, ctypes.c_int32, npost)
+    pre = _arr(lay.shim_pre, ctypes.c_int32, 3 * npre).reshape(-1, 3)
+    cross = _arr(lay.shim_cross, ctypes.c_int32, 4 * ncross).reshape(-1, 4)
+    csite = _arr(lay.shim_csite, ctypes.c_int32, 3 * ncsite).reshape(-1, 3)
+    ptab = _arr(lay.shim_ptab, ctypes.c_uint16, npost_pad * nlo).reshape(npost_pad, nlo).astype(np.int64)
+    xtab = _arr(lay.shim_xtab, ctypes.c_uint16, nslot * nlo).reshape(nslot, nlo).astype(np.int64)
+    order = _arr(lay.shim_order, ctypes.c_uint32, norder)
+    # postfix diagonal per class position (the kernel's dpost table)
+    dpost = np.zeros(nlo)
+    for k in post:
+        i, j = bonds[k]
+        dpost += np.where(((lo_list >> i) & 1) == ((lo_list >> j) & 1), 0.25, -0.25) * J[k]
+    jcross = 0.25 * sum(J[c[2]] for c in cross)
+    pc = np.zeros(npost_pad)
+    pc[:npost] = 0.5 * J[post]
+    y = np.zeros_like(x)
+    for h in order.tolist():
+        m = nup - bin(h).count("1")
+        l0, n, off = int(lo_off[m]), int(lo_off[m + 1] - lo_off[m]), int(hi_off[h])
+        xs = np.zeros(maxblk + 1)
+        xs[:n] = x[off:off + n]
+        g = l0 + np.arange(n)
+        acc = (pc[:, None] * xs[ptab[:, g]]).sum(axis=0)
+        dpre = 0.0
+        for a, b, k in pre:
+            if ((h >> a) & 1) != ((h >> b) & 1):
+                dpre -= 0.25 * J[k]
+                o2 = int(hi_off[h ^ (1 << a) ^ (1 << b)])
+                acc += 0.5 * J[k] * x[o2:o2 + n]
+            else:
+                dpre += 0.25 * J[k]
+        l = lo_list[g]
+        for a, q0, q1 in csite:
+            hb = (h >> a) & 1
+            o2 = int(hi_off[h ^ (1 << a)])
+            for q in range(q0, q1):
+                site, k, slot = cross[q][1], cross[q][2], cross[q][3]
+                f = ((l >> site) & 1) == (1 - hb)
+                tgt = np.where(f, o2 + xtab[slot, g], 0)  # read only where the bond flips
+                acc += np.where(f, 0.5 * J[k] * (x[tgt] - xs[:n]), 0.0)
+        y[off:off + n] = (dpre + jcross + dpost[g]) * xs[:n] + acc
+    return y
+
+
+@pytest.mark.parametrize("case", range(5))
+def test_block_tables_reproduce_the_product(lay, orc, case):
+    from paper_2505_02901_gb300 import workloads as W
+    rng = np.random.default_rng(case)
+    if case == 0:
+        N, nup, bonds = 20, 10, W.random_bonds(20, 45, 3)
+    elif case == 1:
+        N, nup, bonds = 20, 10, W.square_j1j2(4, 5)[0]
+    elif case == 2:
+        N, nup, bonds = 20, 9, W.ladder(10, 2)
+    elif case == 3:
+        N, nup, bonds = 22, 11, W.chain(22)
+    else:
+        N, nup, bonds = 24, 4, W.random_bonds(24, 60, 8)
+    J = rng.uniform(0.5, 1.5, len(bonds))
+    st = orc.enumerate_states(N, nup)
+    x = rng.standard_normal(st.size)
+    y = block_product_twin(lay, N, nup, bonds, J, x)
+    yo = orc.apply_u1(N, st, bonds, J, x)
+    assert np.abs(y - yo).max() <= 1e-12 * np.abs(yo).max()
