@@ -41,9 +41,10 @@ struct U1Layout {
     std::vector<uint32_t> lo_rank, lo_list, lo_off;  // [2^L], [2^L], [L + 2]
 };
 
-// false if the tables do not add up to C(N, nup) (cannot happen for 0 <= nup <= N)
-inline bool u1_layout(int N, int nup, U1Layout *u) {
-    const int L = choose_L(N), P = N - L;
+// The tables at postfix width L; false if they do not add up to C(N, nup)
+// (cannot happen for 0 <= nup <= N).
+inline bool u1_layout_at(int N, int nup, int L, U1Layout *u) {
+    const int P = N - L;
     u->L = L;
     u->P = P;
     const uint64_t nlo = 1ull << L, nhi = 1ull << P;
@@ -66,6 +67,8 @@ inline bool u1_layout(int N, int nup, U1Layout *u) {
     u->dim = u->hi_off[nhi];
     return u->dim == n_choose_k(N, nup);
 }
+
+inline bool u1_layout(int N, int nup, U1Layout *u) { return u1_layout_at(N, nup, choose_L(N), u); }
 
 // index of s, or -1 when s is not a word of the block
 inline int64_t u1_index(int N, int nup, int L, const std::vector<int64_t> &hi_off,
@@ -105,7 +108,7 @@ struct BlockTables {
 };
 
 inline void block_tables(int N, int nup, int L, const int32_t *bonds, int nb, const std::vector<uint32_t> &lo_rank,
-                         const std::vector<uint32_t> &lo_list, BlockTables *out) {
+                         const std::vector<uint32_t> &lo_list, BlockTables *out, bool with_order = true) {
     BlockTables &B = *out;
     const int P = N - L;
     for (int k = 0; k < nb; ++k) {
@@ -147,10 +150,34 @@ inline void block_tables(int N, int nup, int L, const int32_t *bonds, int nb, co
         for (size_t q = 0; q < B.slot_site.size(); ++q)
             B.xtab[q * nlo + g] = (uint16_t)lo_rank[l ^ (1u << B.slot_site[q])];
     }
+    if (with_order)
+        for (uint64_t h = 0; h < (1ull << P); ++h) {
+            const int m = nup - __builtin_popcountll(h);
+            if (m >= 0 && m <= L) B.order.push_back((uint32_t)h);
+        }
+}
+
+// Work items of the batched FP32 product: kB prefixes of one class m each,
+// ascending h within the class; an item is emitted when its class has kB
+// prefixes, and each class's last item is padded with `empty`.
+inline std::vector<uint32_t> prefix_items(int P, int nup, int L, int kB, uint32_t empty) {
+    std::vector<uint32_t> items;
+    std::vector<std::vector<uint32_t>> pend(L + 1);
     for (uint64_t h = 0; h < (1ull << P); ++h) {
         const int m = nup - __builtin_popcountll(h);
-        if (m >= 0 && m <= L) B.order.push_back((uint32_t)h);
+        if (m < 0 || m > L) continue;
+        pend[m].push_back((uint32_t)h);
+        if ((int)pend[m].size() == kB) {
+            items.insert(items.end(), pend[m].begin(), pend[m].end());
+            pend[m].clear();
+        }
     }
+    for (auto &v : pend)
+        if (!v.empty()) {
+            items.insert(items.end(), v.begin(), v.end());
+            items.insert(items.end(), kB - v.size(), empty);
+        }
+    return items;
 }
 
 }  // namespace xd

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "xd_internal.cuh"
+#include "xd_layout.h"
 
 namespace xd {
 
@@ -408,13 +409,6 @@ __global__ void k_pcsr_fill(int P, int nup, int L, const int32_t *__restrict__ p
     }
 }
 
-int64_t binom64(int n, int k) {
-    if (k < 0 || k > n) return 0;
-    int64_t r = 1;
-    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
-    return r;
-}
-
 int spmm_L(int N) { return std::min(12, N - 12); }
 
 }  // namespace
@@ -431,94 +425,29 @@ xd_status spmm_layout_build(xd_basis_s *b) {
     const int L = spmm_L(N), P = N - L;
     s.L = L;
     s.P = P;
-    const uint32_t nlo = 1u << L;
-    // U(1) two-table layout at this L
-    s.h_lo_off.assign(L + 2, 0);
-    for (int m = 0; m <= L; ++m) s.h_lo_off[m + 1] = s.h_lo_off[m] + (uint32_t)binom64(L, m);
-    std::vector<uint32_t> lo_rank(nlo), lo_list(nlo);
-    {
-        std::vector<uint32_t> fill(s.h_lo_off.begin(), s.h_lo_off.end() - 1);
-        for (uint32_t l = 0; l < nlo; ++l) {
-            const int m = __builtin_popcount(l);
-            const uint32_t r = fill[m]++ - s.h_lo_off[m];
-            lo_rank[l] = r;
-            lo_list[s.h_lo_off[m] + r] = l;
-        }
-    }
-    s.h_lo_list = lo_list;
-    std::vector<int64_t> hi_off((1ull << P) + 1, 0);
-    for (uint64_t h = 0; h < (1ull << P); ++h) {
-        const int m = nup - __builtin_popcountll(h);
-        hi_off[h + 1] = hi_off[h] + ((m >= 0 && m <= L) ? binom64(L, m) : 0);
-    }
-    // bond classes
-    std::vector<int32_t> pre, cross, csite;
-    std::vector<uint16_t> postid;
-    std::vector<int> slot_site;
-    for (int k = 0; k < b->nb; ++k) {
-        int i = std::min(b->bonds[k].i, b->bonds[k].j), j = std::max(b->bonds[k].i, b->bonds[k].j);
-        if (j < L) {
-            postid.push_back((uint16_t)k);
-        } else if (i >= L) {
-            pre.insert(pre.end(), {i - L, j - L, k});
-        } else {
-            int slot = (int)(std::find(slot_site.begin(), slot_site.end(), i) - slot_site.begin());
-            if (slot == (int)slot_site.size()) slot_site.push_back(i);
-            cross.insert(cross.end(), {j - L, i, k, slot});
-        }
-    }
-    {
-        const int nc = (int)cross.size() / 4;
-        std::vector<int> idx(nc);
-        for (int q = 0; q < nc; ++q) idx[q] = q;
-        std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return cross[4 * a] < cross[4 * c]; });
-        std::vector<int32_t> sorted;
-        for (int q : idx) sorted.insert(sorted.end(), cross.begin() + 4 * q, cross.begin() + 4 * q + 4);
-        cross.swap(sorted);
-        for (int q = 0; q < nc; ++q)
-            if (q == 0 || cross[4 * q] != cross[4 * (q - 1)]) csite.insert(csite.end(), {cross[4 * q], q, q + 1});
-            else csite.back() = q + 1;
-    }
-    s.post.assign(postid.begin(), postid.end());
-    s.npost = (int)postid.size();
-    s.npost_pad = (s.npost + 7) / 8 * 8;
+    // U(1) two-table layout at this L, bond classes and target tables
+    U1Layout lay;
+    u1_layout_at(N, nup, L, &lay);
+    BlockTables T;
+    block_tables(N, nup, L, (const int32_t *)b->bonds.data(), b->nb, lay.lo_rank, lay.lo_list, &T, false);
+    s.h_lo_off = lay.lo_off;
+    s.h_lo_list = lay.lo_list;
+    const std::vector<uint32_t> &lo_list = lay.lo_list;
+    const std::vector<int64_t> &hi_off = lay.hi_off;
+    const std::vector<int32_t> &pre = T.pre, &cross = T.cross, &csite = T.csite;
+    const std::vector<uint16_t> &ptab = T.ptab, &xtab = T.xtab;
+    s.post.assign(T.post.begin(), T.post.end());
+    s.npost = (int)T.post.size();
+    s.npost_pad = T.npost_pad;
     s.npre = (int)pre.size() / 3;
     s.ncross = (int)cross.size() / 4;
     s.ncsite = (int)csite.size() / 3;
-    s.maxblk = (int)binom64(L, L / 2);
+    s.maxblk = T.maxblk;
     s.cross_ids.clear();
     for (int q = 0; q < s.ncross; ++q) s.cross_ids.push_back(cross[4 * q + 2]);
-    // target tables indexed by the class position of the postfix word
-    const uint16_t noflip = (uint16_t)s.maxblk;
-    std::vector<uint16_t> ptab((size_t)s.npost_pad * nlo, noflip), xtab((size_t)slot_site.size() * nlo);
-    for (uint32_t g = 0; g < nlo; ++g) {
-        const uint32_t l = lo_list[g];
-        for (int q = 0; q < s.npost; ++q) {
-            const int i = b->bonds[postid[q]].i, j = b->bonds[postid[q]].j;
-            if (((l >> i) & 1) != ((l >> j) & 1)) ptab[(size_t)q * nlo + g] = (uint16_t)lo_rank[l ^ (1u << i) ^ (1u << j)];
-        }
-        for (size_t q = 0; q < slot_site.size(); ++q) xtab[q * nlo + g] = (uint16_t)lo_rank[l ^ (1u << slot_site[q])];
-    }
+    std::vector<uint16_t> postid(T.post.begin(), T.post.end());
     postid.resize(s.npost_pad, 0);
-    // work items: kB prefixes of one class, in ascending h
-    std::vector<uint32_t> items;
-    {
-        std::vector<std::vector<uint32_t>> pend(L + 1);
-        for (uint64_t h = 0; h < (1ull << P); ++h) {
-            const int m = nup - __builtin_popcountll(h);
-            if (m < 0 || m > L) continue;
-            pend[m].push_back((uint32_t)h);
-            if ((int)pend[m].size() == kB) {
-                items.insert(items.end(), pend[m].begin(), pend[m].end());
-                pend[m].clear();
-            }
-        }
-        for (auto &v : pend)
-            if (!v.empty()) {
-                items.insert(items.end(), v.begin(), v.end());
-                items.insert(items.end(), kB - v.size(), kEmpty);
-            }
-    }
+    const std::vector<uint32_t> items = prefix_items(P, nup, L, kB, kEmpty);
     s.nitems = (int64_t)items.size() / kB;
     auto up = [](auto **dst, const auto &v) -> xd_status {
         using E = typename std::remove_reference<decltype(v)>::type::value_type;

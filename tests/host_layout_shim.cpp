@@ -24,10 +24,10 @@ extern "C" unsigned long long shim_u1_state(long long idx) {
 static xd::BlockTables g_blk;
 
 // sizes: L, npost, npre, ncross, ncsite, nslot, npost_pad, maxblk, norder
-extern "C" void shim_block_build(int N, int nup, const int32_t *bonds, int nb, int *sizes) {
+extern "C" void shim_block_build_at(int N, int nup, int L, const int32_t *bonds, int nb, int *sizes) {
     g_N = N;
     g_nup = nup;
-    xd::u1_layout(N, nup, &g_lay);
+    xd::u1_layout_at(N, nup, L > 0 ? L : xd::choose_L(N), &g_lay);
     g_blk = xd::BlockTables();
     xd::block_tables(N, nup, g_lay.L, bonds, nb, g_lay.lo_rank, g_lay.lo_list, &g_blk);
     const int s[9] = {g_lay.L, (int)g_blk.post.size(), (int)g_blk.pre.size() / 3, (int)g_blk.cross.size() / 4,
@@ -46,3 +46,13 @@ extern "C" const int32_t *shim_csite() { return g_blk.csite.data(); }
 extern "C" const uint16_t *shim_ptab() { return g_blk.ptab.data(); }
 extern "C" const uint16_t *shim_xtab() { return g_blk.xtab.data(); }
 extern "C" const uint32_t *shim_order() { return g_blk.order.data(); }
+
+extern "C" void shim_block_build(int N, int nup, const int32_t *bonds, int nb, int *sizes) {
+    shim_block_build_at(N, nup, 0, bonds, nb, sizes);
+}
+
+extern "C" long long shim_items(int P, int nup, int L, int kB, uint32_t empty, uint32_t *out, long long cap) {
+    const std::vector<uint32_t> v = xd::prefix_items(P, nup, L, kB, empty);
+    for (size_t i = 0; i < v.size() && (long long)i < cap; ++i) out[i] = v[i];
+    return (long long)v.size();
+}

@@ -70,7 +70,7 @@ def _arr(fn, ctype, n):
     return np.ctypeslib.as_array(fn(), shape=(max(1, n),))[:n].copy() if n else np.zeros(0)
 
 
-def block_product_twin(lay, N, nup, bonds, J, x):
+def block_product_twin(lay, N, nup, bonds, J, x, L_at=0):
     """y = H x read off the block tables the way the FP64 block kernel uses
     them: per prefix block h, postfix flips through ptab (the zero slot for
     "no flip"), prefix flips as whole neighbour blocks at the same position,
@@ -79,7 +79,7 @@ def block_product_twin(lay, N, nup, bonds, J, x):
     and postfix terms."""
     bonds = np.ascontiguousarray(bonds, dtype=np.int32)
     sz = (ctypes.c_int * 9)()
-    lay.shim_block_build(N, nup, bonds.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(bonds), sz)
+    lay.shim_block_build_at(N, nup, L_at, bonds.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(bonds), sz)
     L, npost, npre, ncross, ncsite, nslot, npost_pad, maxblk, norder = list(sz)
     P, nlo = N - L, 1 << L
     hi_off = _arr(lay.shim_hi_off, ctypes.c_int64, (1 << P) + 1)
@@ -149,3 +149,44 @@ def test_block_tables_reproduce_the_product(lay, orc, case):
     y = block_product_twin(lay, N, nup, bonds, J, x)
     yo = orc.apply_u1(N, st, bonds, J, x)
     assert np.abs(y - yo).max() <= 1e-12 * np.abs(yo).max()
+
+
+@pytest.mark.parametrize("N,nup", [(24, 12), (26, 7)])
+def test_tables_at_the_batched_width(lay, orc, N, nup):
+    """The FP32 batched product keeps a postfix of L = min(12, N - 12) bits;
+    its tables (same construction at that L) reproduce the product."""
+    from paper_2505_02901_gb300 import workloads as W
+    bonds = W.square_j1j2(4, N // 4)[0] if N % 4 == 0 else W.random_bonds(N, 2 * N, 5)
+    rng = np.random.default_rng(N)
+    J = rng.uniform(0.5, 1.5, len(bonds))
+    st = orc.enumerate_states(N, nup)
+    x = rng.standard_normal(st.size)
+    y = block_product_twin(lay, N, nup, bonds, J, x, L_at=min(12, N - 12))
+    yo = orc.apply_u1(N, st, bonds, J, x)
+    assert np.abs(y - yo).max() <= 1e-12 * np.abs(yo).max()
+
+
+@pytest.mark.parametrize("N,nup", [(24, 12), (28, 14), (30, 3), (26, 20)])
+def test_work_items(lay, N, nup):
+    """Every prefix with a non-empty block appears in exactly one item; an
+    item holds kB prefixes of one class, ascending, padded only at its end."""
+    L = min(12, N - 12)
+    P, kB, empty = N - L, 8, 0xFFFFFFFF
+    lay.shim_items.restype = ctypes.c_longlong
+    lay.shim_items.argtypes = [ctypes.c_int] * 4 + [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32), ctypes.c_longlong]
+    n = lay.shim_items(P, nup, L, kB, empty, None, 0)
+    out = np.zeros(n, dtype=np.uint32)
+    assert lay.shim_items(P, nup, L, kB, empty, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), n) == n
+    assert n % kB == 0
+    want = [h for h in range(1 << P) if 0 <= nup - bin(h).count("1") <= L]
+    got = [int(h) for h in out if h != empty]
+    assert sorted(got) == want
+    last = {}
+    for it in out.reshape(-1, kB):
+        real = [int(h) for h in it if h != empty]
+        assert real and all(h == empty for h in it[len(real):])  # padding at the end only
+        cls = {nup - bin(h).count("1") for h in real}
+        assert len(cls) == 1
+        m = cls.pop()
+        assert real == sorted(real) and real[0] > last.get(m, -1)
+        last[m] = real[-1]
