@@ -196,9 +196,16 @@ xd_status autotune(Plan *p) {
     }
     const int cand_threads[] = {128, 256, 512};
     const int cand_rows_per_thread[] = {1, 4, 16};
-    cudaEvent_t e0, e1;
-    XD_CUDA(cudaEventCreate(&e0));
-    XD_CUDA(cudaEventCreate(&e1));
+    struct Events {  // destroyed on every return path
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~Events() {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } ev;
+    XD_CUDA(cudaEventCreate(&ev.a));
+    XD_CUDA(cudaEventCreate(&ev.b));
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
     float best = 1e30f;
     int bt = 256, br = 1024;
     for (int th : cand_threads)
@@ -220,8 +227,6 @@ xd_status autotune(Plan *p) {
                 br = th * rpt;
             }
         }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     p->threads = bt;
     p->tile_rows = br;
     XD_TRY(build_table(p));
