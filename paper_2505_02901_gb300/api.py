@@ -12,7 +12,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import XD_C128, XD_F32, XD_F64, XDError, check
+from ._lib import XD_C128, XD_EINVAL, XD_F32, XD_F64, XDError, check
 
 _DT = {torch.float64: XD_F64, torch.float32: XD_F32, torch.complex128: XD_C128}
 
@@ -87,15 +87,48 @@ class Basis:
 
     def correlations(self, psi: torch.Tensor, pairs, kind: str = "ss") -> np.ndarray:
         """<psi| O_ij |psi> for every site pair, O = S_i.S_j (kind "ss") or
-        Sz_i Sz_j (kind "zz") (Sec. 3.7 inner); U(1) blocks."""
+        Sz_i Sz_j (kind "zz") (Sec. 3.7 inner).  U(1) blocks: both kinds.
+        Symmetry-adapted blocks: kind "ss", through the symmetric bond form
+        on the orbits of the pairs (psi normalised)."""
         _check_vec(psi, self.dim, "psi")
         p = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        if self.symmetric:
+            return self._orbit_correlations(psi, p, kind)
         out = np.zeros(p.shape[0])
         torch.cuda.current_stream().synchronize()
         check(_lib.lib().xd_correlations(self._h, _ptr(psi), _dtype_code(psi),
                                          p.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), p.shape[0],
                                          {"zz": 0, "ss": 1}[kind], out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out
+
+    def _orbit_correlations(self, psi, p, kind):
+        """Within a one-dimensional irrep <psi|S_i.S_j|psi> is the same on every
+        site pair of one orbit of the group (Sec. 3.10), which is what the
+        symmetric bond form returns per bond.  The pairs' orbits become the
+        bonds of an auxiliary block of the same group and irrep (the same
+        representatives, so psi is a vector of it) with unit couplings."""
+        if kind != "ss":
+            raise XDError(XD_EINVAL, "correlations: symmetry-adapted blocks give S_i.S_j only (kind 'ss')")
+        if p.size and (p.min() < 0 or p.max() >= self.N):
+            raise XDError(XD_EINVAL, f"correlations: site pairs must lie in 0..{self.N - 1}")
+        key = lambda i, j: (min(i, j), max(i, j))  # noqa: E731
+        bonds, where = [], {}
+        for i, j in p.tolist():
+            if i == j or key(i, j) in where:
+                continue
+            for g in self._perms:
+                e = key(int(g[i]), int(g[j]))
+                if e not in where:
+                    where[e] = len(bonds)
+                    bonds.append(e)
+        f = None
+        if bonds:
+            aux = Basis(self.N, self.nup, np.array(bonds, dtype=np.int32),
+                        symmetry=(self._perms, self._cr + 1j * self._ci))
+            if aux.dim != self.dim:
+                raise RuntimeError("auxiliary block of the pair orbits has another dimension")
+            f = Hamiltonian(aux, np.ones(len(bonds))).bilinear(psi, psi).cpu().numpy()
+        return np.array([0.75 if i == j else f[where[key(i, j)]] for i, j in p.tolist()])
 
     def __del__(self):
         h = getattr(self, "_h", None)
