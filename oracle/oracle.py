@@ -324,20 +324,23 @@ def lanczos(matvec, dim: int, v0: np.ndarray, steps: int, full_reorth: bool = Tr
     """Lanczos tridiagonalisation (Sec. 3.6.1) in FP64 from the start v0.
 
     Returns (alpha, beta) with T = tridiag(beta[:-1], alpha, beta[:-1]).
-    With full_reorth the new vector is orthogonalised against all earlier
-    ones twice (classical Gram-Schmidt, repeated)."""
-    v = np.asarray(v0, dtype=np.float64) / np.linalg.norm(v0)
+    Complex vectors (the blocks of complex characters) take the Hermitian
+    inner product <v|w>, which is real for a Hermitian H.  With full_reorth
+    the new vector is orthogonalised against all earlier ones twice
+    (classical Gram-Schmidt, repeated)."""
+    v0 = np.asarray(v0)
+    v = v0.astype(np.complex128 if np.iscomplexobj(v0) else np.float64) / np.linalg.norm(v0)
     V = [v]
     alpha, beta = [], []
     b_prev, v_prev = 0.0, np.zeros_like(v)
     for k in range(steps):
         w = matvec(v) - b_prev * v_prev
-        a = float(np.dot(w, v))
+        a = float(np.vdot(v, w).real)
         w = w - a * v
         if full_reorth:
             for _ in range(2):
                 Vm = np.array(V)
-                w = w - Vm.T @ (Vm @ w)
+                w = w - Vm.T @ (Vm.conj() @ w)
         b = float(np.linalg.norm(w))
         alpha.append(a)
         beta.append(b)

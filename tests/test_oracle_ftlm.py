@@ -44,3 +44,18 @@ def test_random_starts_high_temperature_and_ground_state(orc):
     (_, e_hi, _), (_, e_lo, _) = orc.ftlm_thermo(tri, st.size, [1e4, 0.02])
     assert abs(e_hi - w.mean()) < 0.05 * np.abs(w).max()
     assert abs(e_lo - w[0]) < 1e-6
+
+
+def test_lanczos_on_a_complex_block(orc):
+    """The oracle's Lanczos on a complex (momentum 2 pi / 12) block of the
+    chain: Hermitian inner products, real tridiagonal, its extreme Ritz
+    values equal to numpy's eigenvalues of the dense block."""
+    from paper_2505_02901_gb300 import workloads as W
+    blk = orc.SymBlock(12, 6, W.chain_translations(12), W.chain_characters(12, 1))
+    H = blk.dense(W.chain(12), np.ones(12))
+    assert np.abs(H.imag).max() > 1e-3 and np.abs(H - H.conj().T).max() < 1e-14
+    a, b = orc.lanczos(lambda v: H @ v, blk.dim, orc.rng_normal(3, 0, blk.dim).astype(complex), 60)
+    assert a.dtype == np.float64 and b.dtype == np.float64
+    T = np.diag(a) + np.diag(b[:-1], 1) + np.diag(b[:-1], -1)
+    w, wt = np.linalg.eigvalsh(H), np.sort(np.linalg.eigvalsh(T))
+    assert np.abs(wt[:3] - w[:3]).max() < 1e-12 and abs(wt[-1] - w[-1]) < 1e-12
