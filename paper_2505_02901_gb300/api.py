@@ -223,10 +223,22 @@ class Hamiltonian:
 
     def ftlm(self, R: int = 16, M: int = 80, seed: int = 1):
         """Finite-temperature Lanczos tridiagonals of R random starts (seed + r),
-        M steps each; returns (alpha [R, M], beta [R, M], n_iter [R])."""
+        M steps each; returns (alpha [R, M], beta [R, M], n_iter [R]).  U(1)
+        blocks run eight starts at a time on the eight-vector product;
+        symmetry-adapted blocks run one Lanczos pass per start on their own
+        product (the same seeded starts)."""
+        if R < 1 or M < 1:
+            raise XDError(XD_EINVAL, "ftlm: need R >= 1 and M >= 1")
         a = np.zeros((R, M))
         b = np.zeros((R, M))
         n = np.zeros(R, dtype=np.int32)
+        if self.basis.symmetric:
+            storage = torch.complex128 if self.basis.is_complex else torch.float64
+            for r in range(R):
+                info = self._lanczos(M, seed + r, storage, 1)
+                k = info["n_iter"]
+                a[r, :k], b[r, :k], n[r] = info["alpha"], info["beta"], k
+            return a, b, n
         torch.cuda.current_stream().synchronize()
         dp = ctypes.POINTER(ctypes.c_double)
         check(_lib.lib().xd_ftlm(self._h, int(R), int(M), ctypes.c_uint64(seed), a.ctypes.data_as(dp),

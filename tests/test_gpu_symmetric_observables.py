@@ -1,6 +1,8 @@
-"""Two-point spin correlations on symmetry-adapted blocks on the GPU: the
-symmetric bond form on the orbits of the site pairs, against the oracle's
-U(1) correlations of the lifted state."""
+"""Observables of symmetry-adapted blocks on the GPU: two-point spin
+correlations (the symmetric bond form on the orbits of the site pairs)
+against the oracle's U(1) correlations of the lifted state, and the
+finite-temperature Lanczos tridiagonals against the oracle's Lanczos on the
+dense block from the same seeded starts."""
 import numpy as np
 import pytest
 import torch
@@ -41,3 +43,27 @@ def test_symmetric_block_correlations(orc, case):
     assert np.abs(got - want).max() < 1e-10
     with pytest.raises(A.XDError):
         basis.correlations(psi, pairs, "zz")
+
+
+@pytest.mark.parametrize("case", [0, 2])
+def test_symmetric_block_ftlm(orc, case):
+    A = api()
+    N, nup, bonds, J, perms, chi = _sym_case(case)
+    basis = A.Basis(N, nup, bonds, symmetry=(perms, chi))
+    ham = A.Hamiltonian(basis, J)
+    R, M, seed = 5, 12, 40
+    a, b, n = ham.ftlm(R, M, seed)
+    H = orc.SymBlock(N, nup, perms, chi).dense(bonds, J)
+    if not basis.is_complex:
+        H = H.real
+    for r in range(R):
+        start = orc.rng_normal(seed + r, 0, basis.dim)
+        ao, bo = orc.lanczos(lambda v: H @ v, basis.dim, start.astype(H.dtype), M, full_reorth=False, tol=0.0)
+        k = n[r]
+        assert k == M == len(ao)
+        assert np.abs(a[r, :k] - ao).max() <= 1e-9 * np.abs(ao).max()
+        assert np.abs(b[r, :k - 1] - bo[:k - 1]).max() <= 1e-9 * np.abs(bo).max()
+    # thermodynamics from longer runs: the block's ground level at low temperature
+    a, b, n = ham.ftlm(4, 40, seed)
+    Z, E, C = A.ftlm_thermo(a, b, n, basis.dim, [0.01])
+    assert abs(E[0] - np.linalg.eigvalsh(H)[0]) < 1e-8
