@@ -151,7 +151,9 @@ xd_status xd_apply_bilinear(xd_ham h, const void *g, const void *x,
  * rejected with XD_ERANGE (xd_apply_bilinear has no such limit).
  * The first call on each device looks up that array's device address (this
  * may load the library's device code on that device); make that first call
- * before any stream capture.  All calls share the array and it keeps the
+ * before any stream capture.  The address is cached per device index for
+ * the life of the process: after a cudaDeviceReset the cached address is
+ * stale, so do not use this call in a process that resets its devices.  All calls share the array and it keeps the
  * last call's contents, so calls that overlap on the GPU (other streams,
  * other threads) race and must be serialised by the caller.  Asynchronous
  * on `stream`. */
@@ -234,10 +236,13 @@ xd_status xd_ftlm_thermo(int R, int M, const double *alpha, const double *beta,
 xd_status xd_energy_grad(xd_ham h, const void *psi0, xd_dtype dtype,
                          double *dEdJ);
 
-/* Seeded standard-normal vector, entry i = BoxMuller(SplitMix64(seed ^ 2i),
- * SplitMix64(seed ^ (2i+1))) (the random_state of Sec. 3.5 with this
- * project's counter-based generator), unnormalised, written to the device
- * array out [dim] of dtype (XD_C128: real parts, zero imaginary parts).
+/* Seeded standard-normal vector (the random_state of Sec. 3.5 with this
+ * project's counter-based generator): with gamma = 0x9E3779B97F4A7C15 and
+ * SplitMix64(z) the generator's output for state z + gamma, the stream state
+ * is k = SplitMix64(seed) and entry i = BoxMuller(SplitMix64(k + 2i gamma),
+ * SplitMix64(k + (2i+1) gamma)), uniforms (top 53 bits + 1) / 2^53;
+ * unnormalised, written to the device array out [dim] of dtype (XD_C128:
+ * real parts, zero imaginary parts).  Nearby seeds give independent vectors.
  * Asynchronous. */
 xd_status xd_random_vector(int64_t dim, uint64_t seed, void *out,
                            xd_dtype dtype, xd_stream stream);

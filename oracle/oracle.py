@@ -265,8 +265,8 @@ class SymBlock:
         return y
 
     def dense(self, bonds, J):
-        return self.apply(bonds, J, np.eye(self.dim, dtype=np.complex128).T.copy()).T.copy() \
-            if False else np.stack([self.apply(bonds, J, e) for e in np.eye(self.dim, dtype=np.complex128)], axis=1)
+        """The block's matrix, column k = (block product of unit vector k)."""
+        return np.stack([self.apply(bonds, J, e) for e in np.eye(self.dim, dtype=np.complex128)], axis=1)
 
     def lift(self, states: np.ndarray) -> np.ndarray:
         """Columns |r_chi> = N_r^-1 sum_g conj(chi(g)) g|r> in the U(1) basis."""

@@ -126,7 +126,8 @@ uint64_t xo_state_count(int N, int nup, int64_t idx)
 
 /* ------------------------------------------------------- random vectors */
 
-/* SplitMix64 (Steele, Lea, Flood 2014) used as a counter-based hash. */
+/* One step of SplitMix64 (Steele, Lea, Flood 2014) from state z: the output
+ * of the generator whose state is advanced from z to z + gamma. */
 uint64_t xo_splitmix64(uint64_t z)
 {
     z += 0x9E3779B97F4A7C15ull;
@@ -135,14 +136,20 @@ uint64_t xo_splitmix64(uint64_t z)
     return z ^ (z >> 31);
 }
 
-/* Standard normal entry i of the seeded vector: Box-Muller on the uniforms
- * u = (top 53 bits + 1) / 2^53 in (0,1] drawn from splitmix64(seed ^ 2i)
- * and splitmix64(seed ^ (2i+1)).  (The paper draws N(0,1) entries, Sec. 3.5;
- * the generator itself is this project's choice.) */
+/* Standard normal entry i of the seeded vector: Box-Muller on two uniforms
+ * u = (top 53 bits + 1) / 2^53 in (0,1].  The seed is first mixed into a
+ * stream state k = splitmix64(seed); entry i then takes outputs 2i+1 and
+ * 2i+2 of the SplitMix64 stream started at k, i.e. splitmix64(k + 2i*gamma)
+ * and splitmix64(k + (2i+1)*gamma), gamma = 0x9E3779B97F4A7C15.  Mixing the
+ * seed makes the vectors of nearby seeds (seed, seed + 1, ...) independent
+ * draws instead of permutations of one another.  (The paper draws N(0,1)
+ * entries, Sec. 3.5; the generator itself is this project's choice.) */
 double xo_rng_normal(uint64_t seed, int64_t i)
 {
-    uint64_t a = xo_splitmix64(seed ^ (2u * (uint64_t)i));
-    uint64_t b = xo_splitmix64(seed ^ (2u * (uint64_t)i + 1u));
+    const uint64_t gamma = 0x9E3779B97F4A7C15ull;
+    uint64_t k = xo_splitmix64(seed);
+    uint64_t a = xo_splitmix64(k + (2u * (uint64_t)i) * gamma);
+    uint64_t b = xo_splitmix64(k + (2u * (uint64_t)i + 1u) * gamma);
     double u1 = ((double)(a >> 11) + 1.0) * 0x1.0p-53;
     double u2 = ((double)(b >> 11) + 1.0) * 0x1.0p-53;
     return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);

@@ -30,19 +30,26 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// SplitMix64 output for the state advanced from z by its increment.
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
 __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
-    z += 0x9E3779B97F4A7C15ull;
+    z += kGolden;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
 }
 
+// Seeded standard normals: the seed is mixed into the stream state
+// k = splitmix64(seed), entry i takes outputs 2i+1 and 2i+2 of the SplitMix64
+// stream from k and maps them to (0,1] uniforms for Box-Muller.
 template <typename T>
 __global__ void k_random(int64_t n, uint64_t seed, T *__restrict__ out, int stride) {
+    const uint64_t k = splitmix64(seed);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t a = splitmix64(seed ^ (2ull * (uint64_t)i));
-        const uint64_t b = splitmix64(seed ^ (2ull * (uint64_t)i + 1ull));
+        const uint64_t c = k + 2ull * (uint64_t)i * kGolden;
+        const uint64_t a = splitmix64(c);
+        const uint64_t b = splitmix64(c + kGolden);
         const double u1 = ((double)(a >> 11) + 1.0) * 0x1.0p-53;
         const double u2 = ((double)(b >> 11) + 1.0) * 0x1.0p-53;
         const double v = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
