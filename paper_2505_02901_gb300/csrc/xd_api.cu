@@ -435,6 +435,7 @@ static xd_status set_J(xd_ham_s *h, const double *J) {
     if (b->sym && !h->d_symtab) XD_TRY(sym_ham_tables(h));
     if (b->blk.ok) XD_TRY(block_ham_tables(h));
     if (b->spmm.ok) XD_TRY(spmm_ham_tables(h));
+    if (b->spmm.ok) XD_TRY(spmm64_tables(h));
     return XD_OK;
 }
 
@@ -482,6 +483,9 @@ void xd_ham_destroy(xd_ham h) {
     cudaFree(h->d_dpost);
     cudaFree(h->d_sp_dpost);
     cudaFree(h->d_sp_jhalf);
+    cudaFree(h->d_x64_tab);
+    cudaFree(h->d_x64_x);
+    cudaFree(h->d_x64_state);
     cudaFree(h->d_part);
     cudaFree(h->d_scal);
     delete h;

@@ -115,7 +115,7 @@ struct SpmmLayoutHost {
     std::vector<uint32_t> h_lo_off, h_lo_list;
     std::vector<int> post, cross_ids;
     int64_t *d_hi_off = nullptr, *d_pcsr_off = nullptr;
-    uint32_t *d_lo_off = nullptr, *d_lo_list = nullptr, *d_items = nullptr;
+    uint32_t *d_lo_off = nullptr, *d_lo_list = nullptr, *d_lo_rank = nullptr, *d_items = nullptr;
     uint16_t *d_ptab = nullptr, *d_xtab = nullptr, *d_postid = nullptr;
     int32_t *d_pre = nullptr, *d_cross = nullptr, *d_csite = nullptr;
     uint64_t *d_pcsr = nullptr;
@@ -173,6 +173,19 @@ struct xd_ham_s {
     float *d_sp_dpost = nullptr;    // batched layout: postfix diagonal per class position
     float *d_sp_jhalf = nullptr;    // batched layout: J/2 per bond
     float sp_jcross = 0.f;          // batched layout: sum over cross bonds of J/4
+    // FP64 product on the batched layout without FP64 arithmetic per element
+    // (xd_u1_spmm64.cu): fixed point when the couplings are small integer
+    // multiples of one quantum, else double-float
+    bool x64_fx_ok = false;         // the couplings have a quantum: fixed point allowed
+    void *d_x64_tab = nullptr;      // one allocation holding the tables below
+    void *d_x64_dfc = nullptr, *d_x64_dfd = nullptr, *d_x64_dfp = nullptr;  // double-float: J/2, J/4, postfix diagonal
+    void *d_x64_fxc = nullptr, *d_x64_fxd = nullptr, *d_x64_fxp = nullptr;  // fixed point: 2 k_b, k_b, postfix D
+    uint32_t *d_x64_post = nullptr; // postfix bond masks | bond << 16
+    double x64_dcross_d = 0.0, x64_qs = 1.0;
+    int x64_dcross_i = 0, x64_B = 0;
+    void *d_x64_x = nullptr;        // workspace, 8 bytes per row (allocated on first use)
+    int *d_x64_state = nullptr;     // [E, mode] and the statistics partials
+    bool x64_unavailable = false;   // the workspace did not fit: FP64 kernels instead
 };
 
 namespace xd {
@@ -205,6 +218,10 @@ xd_status spmm_layout_build(xd_basis_s *b);
 void spmm_layout_free(xd_basis_s *b);
 xd_status spmm_ham_tables(xd_ham_s *h);
 xd_status spmm_apply(const xd_ham_s *h, const void *x, void *y, cudaStream_t st);
+// FP64 product on the same layout, fixed point or double-float (xd_u1_spmm64.cu)
+xd_status spmm64_tables(xd_ham_s *h);
+bool spmm64_usable(const xd_ham_s *h);
+xd_status spmm64_apply(const xd_ham_s *h, const void *x, void *y, cudaStream_t st);
 // eight right-hand sides on the same layout (xd_u1_spmm8.cu); x, y [dim][8] FP32
 bool spmm8_usable(const xd_ham_s *h, const void *x, const void *y);
 xd_status spmm8_apply(const xd_ham_s *h, const void *x, void *y, cudaStream_t st);

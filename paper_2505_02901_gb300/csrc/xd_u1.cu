@@ -242,6 +242,11 @@ static xd_status launch_apply(const xd_ham_s *h, const void *x, void *y, cudaStr
 xd_status u1_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, int nvec,
                    cudaStream_t st) {
     if (nvec == 1 && dt == XD_F32 && h->b->spmm.ok) return spmm_apply(h, x, y, st);
+    if (nvec == 1 && dt == XD_F64 && spmm64_usable(h)) {
+        const xd_status s = spmm64_apply(h, x, y, st);
+        // a workspace that does not fit sends the product to the FP64 kernels
+        if (s != XD_ENOMEM || !h->x64_unavailable) return s;
+    }
     if (nvec == 8 && dt == XD_F32 && spmm8_usable(h, x, y)) return spmm8_apply(h, x, y, st);
     if (nvec == 1 && h->b->blk.ok) return block_apply(h, x, y, dt, st);
     if (dt == XD_F64) {

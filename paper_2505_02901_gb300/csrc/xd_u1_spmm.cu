@@ -458,6 +458,7 @@ xd_status spmm_layout_build(xd_basis_s *b) {
     XD_TRY(up(&s.d_hi_off, hi_off));
     XD_TRY(up(&s.d_lo_off, s.h_lo_off));
     XD_TRY(up(&s.d_lo_list, lo_list));
+    XD_TRY(up(&s.d_lo_rank, lay.lo_rank));
     XD_TRY(up(&s.d_items, items));
     XD_TRY(up(&s.d_ptab, ptab));
     XD_TRY(up(&s.d_xtab, xtab));
@@ -507,6 +508,7 @@ void spmm_layout_free(xd_basis_s *b) {
     cudaFree(s.d_hi_off);
     cudaFree(s.d_lo_off);
     cudaFree(s.d_lo_list);
+    cudaFree(s.d_lo_rank);
     cudaFree(s.d_items);
     cudaFree(s.d_ptab);
     cudaFree(s.d_xtab);
