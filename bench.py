@@ -4,10 +4,13 @@
 
 One step is one y = H x through the CUDA library on inputs resident in HBM
 (x and y are 4.8 GB in FP64, 2.4 GB in FP32: larger than L2, so no flush is
-needed between steps).  Reported: Hamiltonian elements applied per second
-(value), compulsory-byte HBM GB/s and its roofline fraction for the apply
-kernel, Lanczos seconds per iteration, an end-to-end number through the
-public API with host buffers, and the CPU oracle timed on a bounded sample.
+needed between steps).  The headline is the FP64 form (the paper's
+precision); the FP32-storage form is reported beside it.  Reported:
+Hamiltonian elements applied per second (value), compulsory-byte HBM GB/s
+and its roofline fraction for the product, Lanczos seconds per iteration,
+ground energies with their stated errors for every Lanczos result, an
+end-to-end number through the public API with host buffers, and the CPU
+oracle timed on a bounded sample.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--form f64|f32]
     python bench.py --impl reference      # the CPU oracle on the host cores
@@ -33,16 +36,27 @@ SEED = 2
 METRIC = "Hamiltonian elements applied/s for H.v at N=32 Sz=0 (4x8 J1-J2)"
 FORM_NOTE = {
     "f32": "FP32 vector storage and FP32 products (Lanczos dots, alpha, beta in FP64-class arithmetic)",
-    "f64": "FP64 vectors, FP64 products (plain form)",
+    "f64": ("FP64 vectors in and out (the paper's precision, FP64 tolerance 1e-12 on every parity test); "
+            "the product without FP64 arithmetic per element: these couplings are integer multiples of "
+            "q = 1/2, so the device takes exact 64-bit fixed-point sums (x rounded to 52 bits of its "
+            "largest entry, double-float when a vector's dynamic range asks for it), one FP64 "
+            "conversion per row"),
 }
-# dram__bytes_read.sum + dram__bytes_write.sum of one apply launch at this
+# dram__bytes_read.sum + dram__bytes_write.sum of one product launch at this
 # workload (ncu, profiles/apply_4x8_*.md); None until measured for the
 # kernel as it stands
-TRAFFIC = {"f32": 71.64e9, "f64": 146.00e9}
+TRAFFIC = {"f32": 71.64e9, "f64": None}
 # the kernel each form's product runs at this workload
-KERNEL = {"f32": "k_spmm<12>", "f64": "k_block_apply<double, 16, 1>"}
+KERNEL = {"f32": "k_spmm<12>", "f64": "k_spmm64<PolFX> (+ k_x64_stats, k_x64_convert)"}
+# kernels of this library launched per product (FP64: statistics, conversion,
+# the fixed-point product and the double-float product, which returns at once)
+LAUNCHES = {"f32": 1, "f64": 4}
 # GB300 HBM3e nominal bandwidth (the measured copy bandwidth is the peak used)
 HBM_NOMINAL_GBS = 7900.0
+
+
+# ground energies of the Lanczos results, each with its stated error
+ENERGIES = {}
 
 
 class _Null:
@@ -148,6 +162,7 @@ def cpu_baseline(seconds: float = 12.0, extras: bool = True):
     cores = oracle.threads()
     total_rows, t_used = rate(seconds, 64 * cores)
     out = {"value": total_rows / t_used * el_per_row, "unit": "elements/s", "cores": cores, "kind": "oracle",
+           "seconds": t_used,
            "host": _host_cpu(),
            "sample": f"{total_rows} random rows of the N=32 block, x from the seeded generator, "
                      f"{t_used:.1f} s (OpenMP over rows)"}
@@ -159,15 +174,17 @@ def cpu_baseline(seconds: float = 12.0, extras: bool = True):
     b16 = W.chain(16)
     t0 = time.perf_counter()
     a16, _ = oracle.lanczos(lambda v: oracle.apply_u1(16, st16, b16, [1.0] * 16, v), st16.size,
-                            oracle.rng_normal(SEED, 0, st16.size), 100)
+                            oracle.rng_normal(1, 0, st16.size), 100)
     lz16 = (time.perf_counter() - t0) / len(a16)
+    e16 = float(oracle.tridiag_eigvals(a16, _)[0])
     # one thread on a smaller sample of the same rows, for the per-core rate
     oracle.threads(1)
     try:
         rows1, t1 = rate(max(1.0, seconds / 6), 256)
     finally:
         oracle.threads(cores)
-    out.update({"single_core_value": rows1 / t1 * el_per_row, "lanczos_chain16_s_per_iter": lz16})
+    out.update({"single_core_value": rows1 / t1 * el_per_row, "lanczos_chain16_s_per_iter": lz16,
+                "lanczos_chain16_e0": e16})
     out["sample"] += f"; one thread: {rows1} rows, {t1:.1f} s"
     return out
 
@@ -234,7 +251,7 @@ def _lanczos_steady(ham, dtype, iters, short=2):
     return (ts[1][0] - ts[0][0]) / max(1, ts[1][1] - ts[0][1])
 
 
-def extra_rows(hbm):
+def extra_rows(hbm, c5=True):
     """One measurement per remaining hot-path row, each on its own workload:
     batched product (64 uneven instances, 8 FP32 right-hand sides), per-bond
     bilinear forms (14-rung ladder, FP64), symmetric products (6x6 J1-J2,
@@ -286,7 +303,24 @@ def extra_rows(hbm):
     row("a8_bilinear_ladder28_f64", ms, 2 * 8 * h.dim, h.dim * 56, bonds=56)
     ms = _event_time(lambda: h.apply(x))
     row("a5_apply_ladder28_f64", ms, 2 * 8 * h.dim, elems(28, 14, 56))
-    del h, g, x
+    del g, x
+    torch.cuda.empty_cache()
+    # C3 energies: ground state by two FP64 Lanczos passes (200 steps), the
+    # backward kernel's dE0/dJ checked by Euler's identity sum_b J_b dE/dJ_b
+    # = E0 and by equal derivatives of the two copies of each rung; the
+    # FP32-storage ground energy against the FP64 one
+    Jl = W.uniform_couplings(56, 3)
+    t0 = time.perf_counter()
+    e0, psi, info = h.ground_state(max_iter=200, seed=3)
+    gs_s = time.perf_counter() - t0
+    grad = h.energy_grad(psi)
+    e32 = float(h.lanczos(max_iter=200, seed=3, storage=torch.float32)["evals"][0])
+    ENERGIES["c3_ladder28"] = {
+        "e0_f64": e0, "lanczos_steps": info["n_iter"], "resid_f64": float(info["resid"][0]),
+        "ground_state_s": gs_s, "euler_identity_rel_err": abs(float(Jl @ grad) - e0) / abs(e0),
+        "rung_copies_max_grad_diff": float(np.abs(grad[28:42] - grad[42:56]).max()),
+        "e0_f32_storage": e32, "f32_vs_f64_rel_err": abs(e32 - e0) / abs(e0)}
+    del h, psi
     torch.cuda.empty_cache()
     # next row 1: eigenvector and observables -- ground state of the N=28
     # chain (two Lanczos passes, FP64) and its <S0.Sj>, <Sz0 Szj> for all j
@@ -353,9 +387,20 @@ def extra_rows(hbm):
         x = torch.randn(basis.dim, dtype=dt, device="cuda")
         y = torch.empty_like(x)
         ms = _event_time(lambda: h.apply(x, out=y), reps=2)
-        row(f"a4p_sym6x6_k{mx}0_{'c128' if basis.is_complex else 'f64'}", ms, (2 * es + 10) * basis.dim,
-            dim=basis.dim, basis_build_s=build_s)
-        del basis, h, x, y
+        tag = f"k{mx}0_{'c128' if basis.is_complex else 'f64'}"
+        row(f"a4p_sym6x6_{tag}", ms, (2 * es + 10) * basis.dim, dim=basis.dim, basis_build_s=build_s)
+        del x, y
+        torch.cuda.empty_cache()
+        if c5:
+            # config 5: 100 Lanczos steps on the momentum block
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = h.lanczos(max_iter=100, seed=SEED, storage=dt)
+            lz = time.perf_counter() - t0
+            ENERGIES[f"c5_sym6x6_{tag}"] = {"e0": float(info["evals"][0]), "lanczos_steps": info["n_iter"],
+                                            "resid": float(info["resid"][0]), "s_per_iter": lz / info["n_iter"],
+                                            "dim": basis.dim}
+        del basis, h
         torch.cuda.empty_cache()
     # next row 4: full space groups of the 36-site tori, fully symmetric irrep
     # (translations times C4v, 288 elements; times C6v, 432 elements)
@@ -379,7 +424,23 @@ def extra_rows(hbm):
     y = torch.empty_like(x)
     ms = _event_time(lambda: h.apply(x, out=y), reps=2)
     row("a5_apply_6x6_u1_f32", ms, 2 * 4 * h.dim, elems(36, 18, 144), dim=h.dim)
-    del h, x, y
+    del x, y
+    torch.cuda.empty_cache()
+    if c5:
+        # config 5: the no-symmetry sector (dim 9,075,135,300) in FP32 vector
+        # storage (three 36 GB vectors), 100 Lanczos steps; its ground energy
+        # against the lowest of the momentum blocks'
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = h.lanczos(max_iter=100, seed=SEED, storage=torch.float32)
+        lz = time.perf_counter() - t0
+        e_u1 = float(info["evals"][0])
+        e_k = min(v["e0"] for k, v in ENERGIES.items() if k.startswith("c5_sym6x6_"))
+        ENERGIES["c5_u1_6x6_f32"] = {"e0": e_u1, "lanczos_steps": info["n_iter"], "resid": float(info["resid"][0]),
+                                     "s_per_iter": lz / info["n_iter"], "dim": h.dim,
+                                     "lowest_momentum_block_e0": e_k,
+                                     "rel_diff_to_momentum_blocks": abs(e_u1 - e_k) / abs(e_k)}
+    del h
     torch.cuda.empty_cache()
     # The paper's largest U(1) Lanczos benchmark: the N=36 Heisenberg chain,
     # Sz=0 (dim 9,075,135,300), one iteration 3.1 s in FP64 on 2304 cores.
@@ -442,17 +503,21 @@ def run_reference(args):
         cpu_baseline(seconds=per_step, extras=False)
     rates = [cpu_baseline(seconds=per_step, extras=k == args.steps - 1) for k in range(max(1, args.steps))]
     value = statistics.mean(r["value"] for r in rates)
+    step_ms = statistics.mean(r["seconds"] for r in rates) * 1e3
     elements = elements_per_matvec(bonds)
     cb = dict(rates[-1])
     cb["value"] = value
     cb["sample"] = f"{len(rates)} steps of about {per_step:.1f} s each; last: " + rates[-1]["sample"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "elements/s",
             "n_gpus": args.gpus, "steps": len(rates), "warmup": args.warmup,
-            "ms_per_step": elements / value * 1e3, "higher_is_better": True,
+            "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "ms_per_full_product_extrapolated": elements / value * 1e3,
             "config": {"workload": WORKLOAD, "dim": math.comb(N, NUP), "bonds": len(bonds),
                        "elements_per_matvec": elements, "seed": SEED,
-                       "form": "CPU oracle, FP64, sampled rows (ms_per_step extrapolated to a full product)",
+                       "form": ("CPU oracle, FP64; each step is a bounded random sample of rows of the "
+                                "product (ms_per_step is that sample's measured time; the full product's "
+                                "time, extrapolated, is ms_per_full_product_extrapolated)"),
                        "parallelism": "host cores"},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0,
@@ -526,7 +591,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--form", default="f32", choices=["f64", "f32"])
+    ap.add_argument("--form", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--no-c5", action="store_true",
+                    help="skip the 100-step Lanczos runs of the 6x6 blocks (about four minutes)")
     ap.add_argument("--lanczos-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only", action="store_true", help="time the headline form only")
@@ -640,6 +707,24 @@ def main():
         }
     fh = forms[head]
     esize = 8 if head == "f64" else 4
+    if rank == 0 and world == 1 and args.lattice == "4x8" and not args.only:
+        # C2 energies: 200 Lanczos steps from the seeded start in FP64 vectors
+        # and in FP32 vector storage (FP64-class dots); their relative
+        # difference is the FP32 form's stated error
+        c2 = {}
+        for form in ("f64", "f32"):
+            dtype = torch.float64 if form == "f64" else torch.float32
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = ham.lanczos(max_iter=200, seed=SEED, storage=dtype, nev=2)
+            c2[form] = (info, time.perf_counter() - t0)
+            torch.cuda.empty_cache()
+        e64, e32 = float(c2["f64"][0]["evals"][0]), float(c2["f32"][0]["evals"][0])
+        ENERGIES["c2_square4x8"] = {
+            "e0_f64": e64, "e0_f32_storage": e32, "f32_vs_f64_rel_err": abs(e32 - e64) / abs(e64),
+            "e1_f64": float(c2["f64"][0]["evals"][1]), "lanczos_steps": c2["f64"][0]["n_iter"],
+            "resid_f64": float(c2["f64"][0]["resid"][0]), "s_f64": c2["f64"][1], "s_f32": c2["f32"][1],
+            "e0_per_site": e64 / N}
     # end to end through the public API with pinned host buffers (headline
     # form): every step copies its x up and its y down.  Double-buffered:
     # step k's upload runs on a copy stream while step k-1 computes, and its
@@ -702,13 +787,25 @@ def main():
         "forms": forms,
         "clocks": clk.summary(),
         "e2e": {"value": whole_job_rate(world, elements, e2e_ms), "unit": "elements/s",
-                "h2d_bytes_per_step": esize * dim, "d2h_bytes_per_step": esize * dim},
-        "gpu_launches": fh["steps"],
+                "h2d_bytes_per_step": esize * dim, "d2h_bytes_per_step": esize * dim,
+                "how": ("public API: torch copy_ of x from pinned host memory to the device, Hamiltonian.apply "
+                        "(xd_apply), torch copy_ of y to pinned host memory; double-buffered on two copy "
+                        "streams, wall clock over the steps")},
+        "gpu_launches": fh["steps"] * LAUNCHES[head],
     }
     if rank == 0 and world == 1 and not args.no_extras and args.lattice == "4x8":
-        line["rows"] = extra_rows(hbm)
+        line["rows"] = extra_rows(hbm, c5=not args.no_c5)
+        gpu16 = line["rows"].get("a6_a7_lanczos_chain16_f64", {}).get("e0")
+        if gpu16 is not None:
+            ENERGIES["c1_chain16"] = {"e0_f64": gpu16, "lanczos_steps": line["rows"]["a6_a7_lanczos_chain16_f64"]["n_iter"]}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
+        e16 = line["cpu_baseline"].get("lanczos_chain16_e0")
+        if e16 is not None and "c1_chain16" in ENERGIES:
+            ENERGIES["c1_chain16"].update({"e0_oracle": e16,
+                                           "rel_err_vs_oracle": abs(ENERGIES["c1_chain16"]["e0_f64"] - e16) / abs(e16)})
+    if ENERGIES:
+        line["energies"] = ENERGIES
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:

@@ -110,6 +110,14 @@ xd_status xd_basis_state(xd_basis b, int64_t idx, uint64_t *s);
  * symmetric block: s must be a representative).  Host call. */
 xd_status xd_basis_index(xd_basis b, uint64_t s, int64_t *idx);
 
+/* State words of the rows [first, first + count) of the block, in row
+ * order (Sec. 3.1: the block's basis states; for a symmetric block its
+ * representatives, Sec. 3.10), written to out [count] uint64 in device (or
+ * host-pinned) memory, caller-owned.  XD_ERANGE when the range leaves the
+ * block.  Asynchronous on `stream`. */
+xd_status xd_basis_states(xd_basis b, int64_t first, int64_t count,
+                          uint64_t *out, xd_stream stream);
+
 void xd_basis_destroy(xd_basis b);
 
 /* ---------------------------------------------------------- Hamiltonian */

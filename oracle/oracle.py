@@ -81,6 +81,9 @@ def _declare(L):
         "xo_sym_basis": (_i64, [_i32, _i32, _i32, _i32p, _f64p, _f64p, _u64p, _i32p]),
         "xo_sym_apply": (None, [_i32, _i32, _i32p, _f64p, _f64p, _i32, _i32p, _f64p,
                                 _u64p, _i32p, _i64, _f64p, _f64p]),
+        "xo_keyed": (ctypes.c_double, [_u64, _u64, _i32]),
+        "xo_sym_apply_rows_keyed": (None, [_i32, _i32, _i32p, _f64p, _f64p, _i32, _i32p, _f64p,
+                                           _u64, _i32, _u64p, _i64, _f64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -226,6 +229,31 @@ def rep(N: int, perms, s: int):
     u, cnt = ctypes.c_int(), ctypes.c_int()
     r = lib().xo_rep(N, p.shape[0], _p(p, _i32p), s, ctypes.byref(u), ctypes.byref(cnt))
     return int(r), u.value, cnt.value
+
+
+def keyed(seed: int, words, cplx: bool = False) -> np.ndarray:
+    """x_w = xo_keyed(seed, w, 0) (+ i xo_keyed(seed, w, 1)) for each word."""
+    f = lib().xo_keyed
+    re = np.array([f(seed, int(w), 0) for w in words])
+    if not cplx:
+        return re
+    return re + 1j * np.array([f(seed, int(w), 1) for w in words])
+
+
+def sym_apply_rows_keyed(N: int, perms, chi, bonds, J, seed: int, cplx: bool, rows) -> np.ndarray:
+    """Rows (given by their representatives) of H x on a symmetry-adapted
+    block, x keyed on the representatives (xo_sym_apply_rows_keyed)."""
+    p = np.ascontiguousarray(np.asarray(perms, dtype=np.int32))
+    c = np.asarray(chi, dtype=np.complex128)
+    cr, ci = _f64(c.real), _f64(c.imag)
+    b, nb = _bonds(bonds)
+    Jv = _f64(J)
+    r = np.ascontiguousarray(np.asarray(rows, dtype=np.uint64))
+    y = np.empty(r.size, dtype=np.complex128)
+    lib().xo_sym_apply_rows_keyed(N, p.shape[0], _p(p, _i32p), _p(cr, _f64p), _p(ci, _f64p), nb, _p(b, _i32p),
+                                  _p(Jv, _f64p), seed, 1 if cplx else 0, _p(r, _u64p), r.size,
+                                  _p(y.view(np.float64), _f64p))
+    return y
 
 
 class SymBlock:

@@ -160,6 +160,19 @@ void xo_rng_fill(uint64_t seed, int64_t first, int64_t n, double *out)
     for (int64_t i = 0; i < n; ++i) out[i] = xo_rng_normal(seed, first + i);
 }
 
+/* Value keyed on a state word w (for vectors of blocks too large to list):
+ * with k = splitmix64(seed), part 0 (real) and part 1 (imaginary) are
+ *   2 u - 1,  u = (splitmix64(k + (2w + part) gamma) >> 11) 2^-53,
+ * uniform in [-1, 1) and exactly representable, so any two implementations
+ * of this definition give identical values. */
+double xo_keyed(uint64_t seed, uint64_t w, int part)
+{
+    const uint64_t gamma = 0x9E3779B97F4A7C15ull;
+    uint64_t k = xo_splitmix64(seed);
+    uint64_t z = xo_splitmix64(k + (2u * w + (uint64_t)part) * gamma);
+    return 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+}
+
 /* ------------------------------------------------------------ H x (U(1)) */
 
 /* y = H x on the U(1) block, pull form: row r of H applied to x (Eq. 1 with
@@ -430,5 +443,48 @@ void xo_sym_apply(int N, int G, const int32_t *perms, const double *chi_re,
         }
         y[2 * r] = yr + diag * x[2 * r];
         y[2 * r + 1] = yi + diag * x[2 * r + 1];
+    }
+}
+
+/* Rows of y = H x on a symmetry-adapted block for a vector given by the keyed
+ * values (x of the representative r is xo_keyed(seed, r, 0) + i
+ * xo_keyed(seed, r, 1), real blocks: imaginary part 0).  For each requested
+ * representative s (which must belong to the block) the row is the pull-form
+ * row of xo_sym_apply, y_s = d(s) x_s + sum_t h_t chi(u_t) sqrt(|Stab(r'_t)| /
+ * |Stab(s)|) x_{r'_t}, with the lookup of r'_t in a list of representatives
+ * replaced by its membership test (sum_{g in Stab(r')} chi(g) != 0) and its
+ * keyed value.  Lets sampled rows of blocks too large to enumerate be
+ * checked.  y is interleaved complex [nrows][2]. */
+void xo_sym_apply_rows_keyed(int N, int G, const int32_t *perms, const double *chi_re,
+                             const double *chi_im, int nb, const int32_t *bonds,
+                             const double *J, uint64_t seed, int cplx,
+                             const uint64_t *rows, int64_t nrows, double *y)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < nrows; ++q) {
+        uint64_t s = rows[q];
+        int cs;
+        xo_rep(N, G, perms, s, NULL, &cs);
+        double yr = 0.0, yi = 0.0, diag = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            int i = bonds[2 * b], j = bonds[2 * b + 1];
+            if (bit(s, i) == bit(s, j)) { diag += 0.25 * J[b]; continue; }
+            diag -= 0.25 * J[b];
+            uint64_t t = s ^ ((uint64_t)1 << i) ^ ((uint64_t)1 << j);
+            int u, cnt;
+            uint64_t rp = xo_rep(N, G, perms, t, &u, &cnt);
+            double sr = 0.0, si = 0.0;
+            for (int g = 0; g < G; ++g)
+                if (xo_act(N, perms + (int64_t)g * N, rp) == rp) { sr += chi_re[g]; si += chi_im[g]; }
+            if (hypot(sr, si) < 1e-6) continue;
+            double xr = xo_keyed(seed, rp, 0), xi = cplx ? xo_keyed(seed, rp, 1) : 0.0;
+            double amp = 0.5 * J[b] * sqrt((double)cnt / (double)cs);
+            double cr = amp * chi_re[u], ci = amp * chi_im[u];
+            yr += cr * xr - ci * xi;
+            yi += cr * xi + ci * xr;
+        }
+        double xr = xo_keyed(seed, s, 0), xi = cplx ? xo_keyed(seed, s, 1) : 0.0;
+        y[2 * q] = yr + diag * xr;
+        y[2 * q + 1] = yi + diag * xi;
     }
 }

@@ -13,6 +13,7 @@ uint64_t xo_state_count(int N, int nup, int64_t idx);
 uint64_t xo_splitmix64(uint64_t z);
 double xo_rng_normal(uint64_t seed, int64_t i);
 void xo_rng_fill(uint64_t seed, int64_t first, int64_t n, double *out);
+double xo_keyed(uint64_t seed, uint64_t w, int part);
 void xo_apply_u1(int N, const uint64_t *states, int64_t dim, int nb,
                  const int32_t *bonds, const double *J, int nvec,
                  const double *x, double *y);
@@ -39,4 +40,8 @@ void xo_sym_apply(int N, int G, const int32_t *perms, const double *chi_re,
                   const double *chi_im, int nb, const int32_t *bonds,
                   const double *J, const uint64_t *reps, const int32_t *stab,
                   int64_t dim, const double *x, double *y);
+void xo_sym_apply_rows_keyed(int N, int G, const int32_t *perms, const double *chi_re,
+                             const double *chi_im, int nb, const int32_t *bonds,
+                             const double *J, uint64_t seed, int cplx,
+                             const uint64_t *rows, int64_t nrows, double *y);
 #endif

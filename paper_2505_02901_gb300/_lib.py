@@ -38,6 +38,7 @@ SIGNATURES = {
     "xd_basis_is_complex": (_i, [_vp, _c.POINTER(_i)]),
     "xd_basis_state": (_i, [_vp, _i64, _c.POINTER(_u64)]),
     "xd_basis_index": (_i, [_vp, _u64, _c.POINTER(_i64)]),
+    "xd_basis_states": (_i, [_vp, _i64, _i64, _vp, _vp]),
     "xd_basis_destroy": (None, [_vp]),
     "xd_ham_create": (_i, [_vp, _dp, _c.POINTER(_vp)]),
     "xd_ham_set_couplings": (_i, [_vp, _dp]),

@@ -85,6 +85,14 @@ class Basis:
         check(_lib.lib().xd_basis_index(self._h, int(s), ctypes.byref(i)))
         return int(i.value)
 
+    def states(self, first: int = 0, count: int | None = None) -> torch.Tensor:
+        """State words of rows [first, first + count) (representatives on a
+        symmetric block) as a CUDA int64 tensor."""
+        count = self.dim - first if count is None else int(count)
+        out = torch.empty(max(count, 0), dtype=torch.int64, device="cuda")
+        check(_lib.lib().xd_basis_states(self._h, int(first), count, _ptr(out), _stream()))
+        return out
+
     def correlations(self, psi: torch.Tensor, pairs, kind: str = "ss") -> np.ndarray:
         """<psi| O_ij |psi> for every site pair, O = S_i.S_j (kind "ss") or
         Sz_i Sz_j (kind "zz") (Sec. 3.7 inner).  U(1) blocks: both kinds.

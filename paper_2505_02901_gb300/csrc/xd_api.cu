@@ -81,6 +81,16 @@ static xd_status dcopy(T **dst, const T *src, size_t n) {
     return XD_OK;
 }
 
+cudaError_t dev_malloc_vec(xd_ham_s *h, void **p, size_t bytes) {
+    cudaError_t e = dev_malloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation && h->d_x64_x) {
+        cudaGetLastError();
+        x64_release(h);
+        e = dev_malloc(p, bytes);
+    }
+    return e;
+}
+
 xd_status ensure_partials(xd_ham_s *h, size_t bytes) {
     if (h->part_bytes >= bytes) return XD_OK;
     if (h->d_part) cudaFree(h->d_part);
@@ -399,6 +409,25 @@ xd_status xd_basis_index(xd_basis b, uint64_t s, int64_t *idx) {
     }
     *idx = c + popc64(w & ((1ull << (k & 63)) - 1));
     return XD_OK;
+}
+
+xd_status xd_basis_states(xd_basis b, int64_t first, int64_t count, uint64_t *out, xd_stream stream) {
+    if (!b || (!out && count > 0)) {
+        set_error("xd_basis_states: NULL argument");
+        return XD_EINVAL;
+    }
+    if (first < 0 || count < 0 || first > b->dim || count > b->dim - first) {
+        set_error("xd_basis_states: rows [%lld, %lld + %lld) outside 0..%lld", (long long)first, (long long)first,
+                  (long long)count, (long long)b->dim);
+        return XD_ERANGE;
+    }
+    if (count == 0) return XD_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (b->sym) {
+        XD_CUDA(cudaMemcpyAsync(out, b->d_reps + first, (size_t)count * sizeof(uint64_t), cudaMemcpyDefault, st));
+        return XD_OK;
+    }
+    return u1_states(b, first, count, out, st);
 }
 
 void xd_basis_destroy(xd_basis b) {

@@ -185,7 +185,6 @@ struct xd_ham_s {
     int x64_dcross_i = 0, x64_B = 0;
     void *d_x64_x = nullptr;        // workspace, 8 bytes per row (allocated on first use)
     int *d_x64_state = nullptr;     // [E, mode] and the statistics partials
-    bool x64_unavailable = false;   // the workspace did not fit: FP64 kernels instead
 };
 
 namespace xd {
@@ -196,6 +195,7 @@ xd_status u1_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt,
                    int nvec, cudaStream_t st);
 xd_status u1_bilinear(const xd_ham_s *h, const void *g, const void *x,
                       xd_dtype dt, double *dJ, cudaStream_t st);
+xd_status u1_states(const xd_basis_s *b, int64_t first, int64_t count, uint64_t *out, cudaStream_t st);
 // symmetric blocks (xd_sym.cu)
 xd_status sym_build(xd_basis_s *b);
 xd_status sym_ham_tables(xd_ham_s *h);
@@ -222,6 +222,11 @@ xd_status spmm_apply(const xd_ham_s *h, const void *x, void *y, cudaStream_t st)
 xd_status spmm64_tables(xd_ham_s *h);
 bool spmm64_usable(const xd_ham_s *h);
 xd_status spmm64_apply(const xd_ham_s *h, const void *x, void *y, cudaStream_t st);
+// free the FP64 product's workspace (the next FP64 product allocates it again)
+void x64_release(xd_ham_s *h);
+// device allocation for a driver's vectors: when it fails, the handle's FP64
+// product workspace is released and the allocation tried once more
+cudaError_t dev_malloc_vec(xd_ham_s *h, void **p, size_t bytes);
 // eight right-hand sides on the same layout (xd_u1_spmm8.cu); x, y [dim][8] FP32
 bool spmm8_usable(const xd_ham_s *h, const void *x, const void *y);
 xd_status spmm8_apply(const xd_ham_s *h, const void *x, void *y, cudaStream_t st);

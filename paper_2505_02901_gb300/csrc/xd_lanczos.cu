@@ -261,7 +261,7 @@ static xd_status lanczos_run(xd_ham_s *h, int max_iter, uint64_t seed, xd_dtype 
     lw.scal = h->d_scal;
     T *buf[3] = {nullptr, nullptr, nullptr};
     for (int k = 0; k < 3; ++k) {
-        cudaError_t e = dev_malloc((void **)&buf[k], std::max<size_t>(vbytes, 16));
+        cudaError_t e = dev_malloc_vec(h, (void **)&buf[k], std::max<size_t>(vbytes, 16));
         if (e != cudaSuccess) {
             for (int q = 0; q < k; ++q) cudaFree(buf[q]);
             return cuda_status(e, "cudaMalloc(Lanczos vectors)");
@@ -377,7 +377,7 @@ static xd_status evolve_run(xd_ham_s *h, const double *psi0, double zr, double z
     const size_t vbytes = (size_t)n * sizeof(double);
     double *buf[3] = {nullptr, nullptr, nullptr};
     for (int k = 0; k < 3; ++k) {
-        cudaError_t e = dev_malloc((void **)&buf[k], std::max<size_t>(vbytes, 16));
+        cudaError_t e = dev_malloc_vec(h, (void **)&buf[k], std::max<size_t>(vbytes, 16));
         if (e != cudaSuccess) {
             for (int q = 0; q < k; ++q) cudaFree(buf[q]);
             return cuda_status(e, "cudaMalloc(evolution vectors)");
@@ -498,7 +498,7 @@ static xd_status ftlm_run(xd_ham_s *h, int R, int M, uint64_t seed, double *alph
     const size_t vbytes = (size_t)n * sizeof(double);
     double *buf[3] = {nullptr, nullptr, nullptr};
     for (int k = 0; k < 3; ++k) {
-        cudaError_t e = dev_malloc((void **)&buf[k], std::max<size_t>(vbytes, 16));
+        cudaError_t e = dev_malloc_vec(h, (void **)&buf[k], std::max<size_t>(vbytes, 16));
         if (e != cudaSuccess) {
             for (int q = 0; q < k; ++q) cudaFree(buf[q]);
             return cuda_status(e, "cudaMalloc(FTLM vectors)");

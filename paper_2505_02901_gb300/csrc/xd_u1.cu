@@ -126,6 +126,20 @@ __global__ void __launch_bounds__(kThreads) k_apply(U1View u, const double *__re
     }
 }
 
+// State words of rows [first, first + count): the block of row r is the last
+// h with hi_off[h] <= r (binary search), its word (h << L) | lo_list[...].
+__global__ void k_states_range(U1View u, int64_t first, int64_t count, uint64_t *__restrict__ out) {
+    const uint64_t nh = 1ull << u.P;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = first + q;
+        const uint64_t h = find_block(u.hi_off, 0, nh - 1, r);
+        const int m = u.nup - __popcll(h);
+        const uint32_t l = __ldg(u.lo_list + __ldg(u.lo_off + m) + (uint32_t)(r - __ldg(u.hi_off + h)));
+        out[q] = (h << u.L) | l;
+    }
+}
+
 // Bonds per launch of the bilinear kernel.
 constexpr int kChunk = 256;
 
@@ -239,13 +253,20 @@ static xd_status launch_apply(const xd_ham_s *h, const void *x, void *y, cudaStr
     return XD_OK;
 }
 
+xd_status u1_states(const xd_basis_s *b, int64_t first, int64_t count, uint64_t *out, cudaStream_t st) {
+    const int grid = grid_for(count, kThreads, 8);
+    k_states_range<<<grid, kThreads, 0, st>>>(b->u1view(), first, count, out);
+    XD_CUDA(cudaGetLastError());
+    return XD_OK;
+}
+
 xd_status u1_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, int nvec,
                    cudaStream_t st) {
     if (nvec == 1 && dt == XD_F32 && h->b->spmm.ok) return spmm_apply(h, x, y, st);
     if (nvec == 1 && dt == XD_F64 && spmm64_usable(h)) {
         const xd_status s = spmm64_apply(h, x, y, st);
-        // a workspace that does not fit sends the product to the FP64 kernels
-        if (s != XD_ENOMEM || !h->x64_unavailable) return s;
+        // a workspace that does not fit sends this product to the FP64 kernels
+        if (s != XD_ENOMEM) return s;
     }
     if (nvec == 8 && dt == XD_F32 && spmm8_usable(h, x, y)) return spmm8_apply(h, x, y, st);
     if (nvec == 1 && h->b->blk.ok) return block_apply(h, x, y, dt, st);

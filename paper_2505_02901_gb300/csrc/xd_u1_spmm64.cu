@@ -783,22 +783,34 @@ constexpr int kStatThreads = 256;
 constexpr int kStatPerSm = 8;
 
 // The workspace (8 bytes per row, the two state words and the partials of
-// the statistics pass) is allocated on first use.  When it does not fit,
-// x64_unavailable is set and the FP64 product takes the FP64 kernels.
+// the statistics pass) is allocated on first use.  When it does not fit, the
+// call returns XD_ENOMEM and this product takes the FP64 kernels; the next
+// product tries again (the drivers that hold several vectors release the
+// workspace when their own vectors do not fit, x64_release).
 static xd_status x64_workspace(xd_ham_s *h, int64_t dim) {
-    if (h->d_x64_x) return XD_OK;
     grid_for(1, 1, 1);
+    if (!h->d_x64_state) {
+        cudaError_t e = dev_malloc((void **)&h->d_x64_state, 16 + (size_t)g_num_sms * kStatPerSm * sizeof(ExpSum));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return XD_ENOMEM;
+        }
+    }
+    if (h->d_x64_x) return XD_OK;
     cudaError_t e = dev_malloc((void **)&h->d_x64_x, (size_t)dim * 8);
-    if (e == cudaSuccess)
-        e = dev_malloc((void **)&h->d_x64_state, 16 + (size_t)g_num_sms * kStatPerSm * sizeof(ExpSum));
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(h->d_x64_x);
         h->d_x64_x = nullptr;
-        h->x64_unavailable = true;
         return XD_ENOMEM;
     }
     return XD_OK;
+}
+
+void x64_release(xd_ham_s *h) {
+    if (h->d_x64_x) {
+        cudaFree(h->d_x64_x);
+        h->d_x64_x = nullptr;
+    }
 }
 
 template <class Pol>
@@ -854,7 +866,7 @@ static xd_status launch64(const xd_ham_s *h, void *y, cudaStream_t st) {
 // the batched layout has L = 12 for every block it is built for (N >= 24)
 bool spmm64_usable(const xd_ham_s *h) {
     const xd_basis_s *b = h->b;
-    return b->spmm.ok && !h->x64_unavailable && b->spmm.L == kL && h->d_x64_tab != nullptr;
+    return b->spmm.ok && b->spmm.L == kL && h->d_x64_tab != nullptr;
 }
 
 // Statistics of x, the choice of arithmetic and the conversion on the

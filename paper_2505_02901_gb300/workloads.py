@@ -272,3 +272,68 @@ def batched_instances(count: int = 64, seed: int = 4, sizes=(18, 20, 22, 24, 26,
         J = rng.uniform(0.5, 1.5, size=bonds.shape[0]).astype(np.float64)
         out.append(dict(N=N, nup=N // 2, kind=kind, bonds=bonds, J=J))
     return out
+
+
+# ------------------------------------------------------------ keyed values
+# A vector of a block too large to list on the host is generated from the
+# block's own state words: with k = SplitMix64(seed), the value of word w is
+#   2 u - 1,  u = (SplitMix64(k + (2w + part) gamma) >> 11) 2^-53,
+# part 0 the real and part 1 the imaginary part (uniform in [-1, 1),
+# exactly representable, so every implementation of this definition gives
+# the same bits).  SplitMix64(z) is the generator's output for state z + gamma.
+GAMMA = 0x9E3779B97F4A7C15
+_M1, _M2 = 0xBF58476D1CE4E5B9, 0x94D049BB133111EB
+
+
+def _splitmix64_np(z: np.ndarray) -> np.ndarray:
+    with np.errstate(over="ignore"):
+        z = z + np.uint64(GAMMA)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(_M1)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(_M2)
+        return z ^ (z >> np.uint64(31))
+
+
+def keyed_values(seed: int, words, cplx: bool = False) -> np.ndarray:
+    """Keyed values of the words (numpy, uint64 arithmetic)."""
+    w = np.asarray(words, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        k = _splitmix64_np(np.array([seed], dtype=np.uint64))[0]
+
+        def part(p):
+            z = _splitmix64_np(k + (np.uint64(2) * w + np.uint64(p)) * np.uint64(GAMMA))
+            return 2.0 * ((z >> np.uint64(11)).astype(np.float64) * 2.0 ** -53) - 1.0
+        re = part(0)
+        return re + 1j * part(1) if cplx else re
+
+
+def _i64(c: int) -> int:
+    return c - (1 << 64) if c >= 1 << 63 else c
+
+
+def keyed_values_torch(seed: int, words, cplx: bool = False):
+    """The same values from a torch int64 tensor of words (any device): the
+    arithmetic wraps modulo 2^64 and right shifts are made logical by masks."""
+    import torch
+
+    def srl(z, s):
+        return (z >> s) & ((1 << (64 - s)) - 1)
+
+    def sm(z):
+        z = z + _i64(GAMMA)
+        z = (z ^ srl(z, 30)) * _i64(_M1)
+        z = (z ^ srl(z, 27)) * _i64(_M2)
+        return z ^ srl(z, 31)
+
+    k = int(keyed_seed_state(seed))
+    w = words.to(torch.int64)
+
+    def part(p):
+        z = sm(_i64(k) + (2 * w + p) * _i64(GAMMA))
+        return 2.0 * (srl(z, 11).to(torch.float64) * 2.0 ** -53) - 1.0
+    re = part(0)
+    return torch.complex(re, part(1)) if cplx else re
+
+
+def keyed_seed_state(seed: int) -> int:
+    """k = SplitMix64(seed) as a Python integer."""
+    return int(_splitmix64_np(np.array([seed], dtype=np.uint64))[0])

@@ -36,6 +36,41 @@ def test_c5b_square6x6_u1_sampled_rows(orc):
 
 
 @pytest.mark.parametrize("mx", [0, 1])
+def test_c5a_square6x6_sampled_rows(orc, mx):
+    """6x6 J1-J2 with its 36 translations at k=(0,0) (real FP64) and
+    k=(pi/3,0) (complex128), ~2.5e8 representatives each, at full size:
+    x keyed on each row's representative word (the block's words from
+    xd_basis_states), y = H x on the GPU; sampled rows (first, last and 3000
+    random ones) against the oracle's row formula of the projector (Sec. 3.10)
+    evaluated from the representatives alone, relative L2 <= 1e-12; every
+    sampled word a valid representative of the block."""
+    A = api()
+    bonds, J = W.square_j1j2(6, 6)
+    perms, chi = W.torus_translations(6, 6), W.torus_characters(6, 6, mx, 0)
+    basis = A.Basis(36, 18, bonds, symmetry=(perms, chi))
+    assert basis.dim == (252091362 if mx == 0 else 252085716)
+    ham = A.Hamiltonian(basis, J)
+    seed = 40 + mx
+    x = W.keyed_values_torch(seed, basis.states(), basis.is_complex)
+    y = ham.apply(x)
+    del x
+    rows = np.concatenate([[0, basis.dim - 1], np.random.default_rng(10 + mx).integers(0, basis.dim, 3000)])
+    rt = torch.from_numpy(rows).cuda()
+    words = basis.states()[rt].cpu().numpy().astype(np.uint64)
+    ys = y[rt].cpu().numpy()
+    del y
+    torch.cuda.empty_cache()
+    for k in (0, 1, 2, 500, 2999):
+        r, u, cnt = orc.rep(36, perms, int(words[k]))
+        assert r == int(words[k])
+    yo = orc.sym_apply_rows_keyed(36, perms, chi, bonds, J, seed, basis.is_complex, words)
+    if not basis.is_complex:
+        yo = yo.real
+    assert rel_l2(ys, yo) <= 1e-12
+    assert np.abs(ys - yo).max() <= 1e-12 * np.abs(yo).max()
+
+
+@pytest.mark.parametrize("mx", [0, 1])
 def test_c5a_square6x6_momentum_blocks(orc, mx):
     """6x6 J1-J2 with its 36 translations at k=(0,0) (real) and k=(pi/3,0)
     (complex): Burnside dimension, sampled representatives valid and

@@ -252,3 +252,57 @@ def test_space_group_6x6_dimensions(orc):
     gamma = sum(orc.burnside_dim(36, 18, sq, W.space_group_characters(6, 6, "square", r, m))
                 for r in (1, -1) for m in (1, -1))
     assert gamma < orc.burnside_dim(36, 18, W.torus_translations(6, 6), W.torus_characters(6, 6, 0, 0))
+
+
+def test_keyed_values_agree_everywhere(orc):
+    """The keyed input generator: the oracle's C definition, the numpy and
+    the torch implementations of workloads.py give identical bits."""
+    torch = pytest.importorskip("torch")
+    w = np.array([0, 1, 2, 3, 12345, 2**35 + 11, 2**40 - 7], dtype=np.uint64)
+    for seed in (0, 7, 2**63 + 5):
+        a = orc.keyed(seed, w, True)
+        b = W.keyed_values(seed, w, True)
+        c = W.keyed_values_torch(seed, torch.from_numpy(w.astype(np.int64)), True).numpy()
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+        assert np.all(np.abs(a.real) <= 1) and np.all(np.abs(a.imag) <= 1)
+
+
+@pytest.mark.parametrize("kind,a,b", CASES)
+def test_sampled_rows_keyed_equal_the_projected_block(orc, kind, a, b):
+    """Rows of the symmetric product for a vector keyed on the
+    representatives, computed from the representatives alone (membership test
+    and keyed values instead of a list), equal the rows of B^H H B x with B
+    the lifted basis of the projector (Sec. 3.10), for every momentum."""
+    N, bonds, J, perms, chis = _case(kind, a, b)
+    nup = N // 2
+    st = orc.enumerate_states(N, nup)
+    H = orc.dense_u1(N, st, bonds, J)
+    for chi in chis:
+        blk = orc.SymBlock(N, nup, perms, chi)
+        if blk.dim == 0:
+            continue
+        cplx = bool(np.abs(np.imag(chi)).max() > 1e-12)
+        B = blk.lift(st)
+        x = orc.keyed(5, blk.reps, cplx)
+        y = B.conj().T @ H @ B @ x
+        yr = orc.sym_apply_rows_keyed(N, perms, chi, bonds, J, 5, cplx, blk.reps)
+        assert np.abs(yr - y).max() <= 1e-13 * max(1.0, np.abs(y).max())
+
+
+def test_sampled_rows_keyed_equal_the_full_product_4x4(orc):
+    """4x4 J1-J2 with its 16 translations (and the 128-element space group at
+    Gamma, where targets whose representative leaves the block drop out):
+    sampled rows by representatives equal the full symmetric product."""
+    bonds, J = W.square_j1j2(4, 4)
+    groups = [(W.torus_translations(4, 4), W.torus_characters(4, 4, mx, my)) for mx, my in ((0, 0), (1, 0), (2, 2))]
+    groups.append((W.torus_space_group(4), None))
+    for perms, chi in groups:
+        if chi is None:
+            chi = np.ones(len(perms))
+        blk = orc.SymBlock(16, 8, perms, chi)
+        cplx = bool(np.abs(np.imag(chi)).max() > 1e-12)
+        x = orc.keyed(9, blk.reps, cplx)
+        y = blk.apply(bonds, J, x)
+        rows = np.random.default_rng(3).choice(blk.dim, min(200, blk.dim), replace=False)
+        yr = orc.sym_apply_rows_keyed(16, perms, chi, bonds, J, 9, cplx, blk.reps[rows])
+        assert np.abs(yr - y[rows]).max() <= 1e-13 * np.abs(y).max()
