@@ -212,6 +212,7 @@ static xd_status check_group(const xd_basis_s *b) {
 static void free_basis(xd_basis_s *b) {
     block_layout_free(b);
     spmm_layout_free(b);
+    pass_layout_free(b);
     cudaFree(b->d_hi_off);
     cudaFree(b->d_lo_rank);
     cudaFree(b->d_lo_list);
@@ -464,7 +465,7 @@ static xd_status set_J(xd_ham_s *h, const double *J) {
     if (b->sym && !h->d_symtab) XD_TRY(sym_ham_tables(h));
     if (b->blk.ok) XD_TRY(block_ham_tables(h));
     if (b->spmm.ok) XD_TRY(spmm_ham_tables(h));
-    if (b->spmm.ok) XD_TRY(spmm64_tables(h));
+    if (b->spmm.ok) XD_TRY(passes_tables(h));
     return XD_OK;
 }
 

@@ -119,6 +119,23 @@ struct SpmmLayoutHost {
     uint16_t *d_ptab = nullptr, *d_xtab = nullptr, *d_postid = nullptr;
     int32_t *d_pre = nullptr, *d_cross = nullptr, *d_csite = nullptr;
     uint64_t *d_pcsr = nullptr;
+    std::vector<int32_t> h_pre, h_csite;  // prefix bond triples, cross site triples
+};
+
+// Passes of the prefix bonds and the work items of the product in passes
+// (xd_u1_passes.cu), built on first use.
+struct PassLayoutHost {
+    bool ok = false, unusable = false;   // unusable: the prefix bonds need more than four windows
+    int npass = 0;
+    int ws[4] = {}, nwb[4] = {};         // window bits and bonds of each pass
+    uint16_t *d_wlist[4] = {}, *d_wrank[4] = {};  // window words by (popcount, value); their ranks
+    uint32_t *d_woff[4] = {}, *d_wdep[4] = {};    // first word per popcount; deposited prefix bits
+    uint32_t *d_wbond[4] = {};           // window mask | bond << 16
+    uint64_t *d_pitems[4] = {};          // other prefix bits | window popcount << 32 | rank chunk << 40
+    int64_t nitems_p[4] = {};
+    std::vector<int> cross_low;          // prefix sites of the cross bonds (lowest in the items' key)
+    uint32_t *d_items[2] = {};           // k_main's items of 4 and of 8 same-class prefixes
+    int64_t nitems[2] = {};
 };
 
 }  // namespace xd
@@ -153,6 +170,7 @@ struct xd_basis_s {
     double *d_chi = nullptr;  // [G][2]
     xd::BlockLayoutHost blk;
     xd::SpmmLayoutHost spmm;
+    xd::PassLayoutHost pass;
 
     xd::U1View u1view() const;
     xd::SymView symview() const;
@@ -174,7 +192,7 @@ struct xd_ham_s {
     float *d_sp_jhalf = nullptr;    // batched layout: J/2 per bond
     float sp_jcross = 0.f;          // batched layout: sum over cross bonds of J/4
     // FP64 product on the batched layout without FP64 arithmetic per element
-    // (xd_u1_spmm64.cu): fixed point when the couplings are small integer
+    // (xd_u1_passes.cu): fixed point when the couplings are small integer
     // multiples of one quantum, else double-float
     bool x64_fx_ok = false;         // the couplings have a quantum: fixed point allowed
     void *d_x64_tab = nullptr;      // one allocation holding the tables below
@@ -218,10 +236,12 @@ xd_status spmm_layout_build(xd_basis_s *b);
 void spmm_layout_free(xd_basis_s *b);
 xd_status spmm_ham_tables(xd_ham_s *h);
 xd_status spmm_apply(const xd_ham_s *h, const void *x, void *y, cudaStream_t st);
-// FP64 product on the same layout, fixed point or double-float (xd_u1_spmm64.cu)
-xd_status spmm64_tables(xd_ham_s *h);
-bool spmm64_usable(const xd_ham_s *h);
-xd_status spmm64_apply(const xd_ham_s *h, const void *x, void *y, cudaStream_t st);
+// FP64 product in passes over prefix blocks on the same layout, fixed point
+// or double-float (xd_u1_passes.cu)
+xd_status passes_tables(xd_ham_s *h);
+bool passes_usable(const xd_ham_s *h);
+xd_status passes_apply_f64(const xd_ham_s *h, const void *x, void *y, cudaStream_t st);
+void pass_layout_free(xd_basis_s *b);
 // free the FP64 product's workspace (the next FP64 product allocates it again)
 void x64_release(xd_ham_s *h);
 // device allocation for a driver's vectors: when it fails, the handle's FP64

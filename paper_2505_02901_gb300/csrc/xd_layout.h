@@ -180,4 +180,161 @@ inline std::vector<uint32_t> prefix_items(int P, int nup, int L, int kB, uint32_
     return items;
 }
 
+
+// ------------------------------------------------------------ prefix passes
+// A prefix bond b (prefix bits a, c) joins block h to block h ^ m_b.  The
+// FP64 product treats the prefix bonds in passes: a pass takes the bonds with
+// both bits in a window S of at most W prefix bits, so that its flips change
+// only the window word of a prefix and a tile over the window words fits in
+// shared memory.  choose_passes covers the prefix bonds by such windows,
+// greedily: each pass takes, among the candidate W-bit sets, the one that
+// covers the most uncovered bonds, ties broken by the fewest bits the
+// remaining bonds touch.  Candidates are every window of W consecutive bits
+// (whole lattice rows when sites are numbered row by row) and the sets grown
+// from every start bit by adding the bit with the most uncovered bonds into
+// the set, then the highest degree, then the lowest index.  At most
+// max_passes passes; bonds left over join the last one (the kernel would
+// then need its window to hold them: callers check every pass bond lies in
+// its window).
+struct PrefixPass {
+    std::vector<int> low;    // the bits placed lowest in the key, ascending
+    std::vector<int> bonds;  // indices of the pass's bonds among the prefix triples
+};
+
+inline std::vector<PrefixPass> choose_passes(int P, const std::vector<int32_t> &pre, int W, int max_passes) {
+    const int n = (int)pre.size() / 3;
+    std::vector<char> cov(n, 0);
+    std::vector<PrefixPass> out;
+    W = std::max(1, std::min(W, P));
+    auto remaining_bits = [&](const std::vector<char> &c) {
+        uint64_t m = 0;
+        for (int q = 0; q < n; ++q)
+            if (!c[q]) m |= (1ull << pre[3 * q]) | (1ull << pre[3 * q + 1]);
+        return __builtin_popcountll(m);
+    };
+    int left = n;
+    while (left > 0 && (int)out.size() < max_passes) {
+        std::vector<int> deg(P, 0);
+        for (int q = 0; q < n; ++q)
+            if (!cov[q]) {
+                ++deg[pre[3 * q]];
+                ++deg[pre[3 * q + 1]];
+            }
+        int best_cnt = -1, best_rem = 1 << 30;
+        uint64_t best_set = 0;
+        auto consider = [&](uint64_t S) {
+            std::vector<char> c2 = cov;
+            int cnt = 0;
+            for (int q = 0; q < n; ++q)
+                if (!cov[q] && ((S >> pre[3 * q]) & 1) && ((S >> pre[3 * q + 1]) & 1)) {
+                    c2[q] = 1;
+                    ++cnt;
+                }
+            const int rem = remaining_bits(c2);
+            if (cnt > best_cnt || (cnt == best_cnt && rem < best_rem)) {
+                best_cnt = cnt;
+                best_rem = rem;
+                best_set = S;
+            }
+        };
+        for (int s0 = 0; s0 + W <= P; ++s0) consider(((W == 64 ? ~0ull : ((1ull << W) - 1))) << s0);
+        for (int start = 0; start < P; ++start) {
+            if (deg[start] == 0 && start != 0) continue;
+            uint64_t S = 1ull << start;
+            for (int k = 1; k < W; ++k) {
+                int bv = -1, bin = -1, bdeg = -1;
+                for (int v = 0; v < P; ++v) {
+                    if ((S >> v) & 1) continue;
+                    int in = 0;
+                    for (int q = 0; q < n; ++q)
+                        if (!cov[q]) {
+                            const int a = pre[3 * q], c = pre[3 * q + 1];
+                            if ((a == v && ((S >> c) & 1)) || (c == v && ((S >> a) & 1))) ++in;
+                        }
+                    if (in > bin || (in == bin && deg[v] > bdeg)) {
+                        bv = v;
+                        bin = in;
+                        bdeg = deg[v];
+                    }
+                }
+                if (bv < 0) break;
+                S |= 1ull << bv;
+            }
+            consider(S);
+        }
+        if (best_cnt <= 0) break;
+        PrefixPass ps;
+        for (int v = 0; v < P; ++v)
+            if ((best_set >> v) & 1) ps.low.push_back(v);
+        for (int q = 0; q < n; ++q)
+            if (!cov[q] && ((best_set >> pre[3 * q]) & 1) && ((best_set >> pre[3 * q + 1]) & 1)) {
+                ps.bonds.push_back(q);
+                cov[q] = 1;
+                --left;
+            }
+        out.push_back(ps);
+    }
+    if (left > 0) {
+        if (out.empty()) {
+            PrefixPass ps;
+            for (int v = 0; v < W; ++v) ps.low.push_back(v);
+            out.push_back(ps);
+        }
+        for (int q = 0; q < n; ++q)
+            if (!cov[q]) out.back().bonds.push_back(q);
+    }
+    return out;
+}
+
+// Visiting blocks in the order of a key that places a set of prefix bits
+// lowest keeps the blocks reached by flipping those bits close together (in
+// L2).  key of prefix h: the bits of `low` (in their order) lowest, then the
+// other bits in ascending order.
+inline uint32_t pass_key(uint32_t h, const std::vector<int> &low, int P) {
+    uint32_t key = 0;
+    int k = 0;
+    uint32_t used = 0;
+    for (int v : low) {
+        key |= ((h >> v) & 1u) << k++;
+        used |= 1u << v;
+    }
+    for (int v = 0; v < P; ++v)
+        if (!((used >> v) & 1)) key |= ((h >> v) & 1u) << k++;
+    return key;
+}
+
+// the prefixes with a non-empty block, in ascending key order
+inline std::vector<uint32_t> ordered_prefixes(int P, int nup, int L, const std::vector<int> &low) {
+    std::vector<std::pair<uint32_t, uint32_t>> kh;
+    for (uint64_t h = 0; h < (1ull << P); ++h) {
+        const int m = nup - __builtin_popcountll(h);
+        if (m >= 0 && m <= L) kh.push_back({pass_key((uint32_t)h, low, P), (uint32_t)h});
+    }
+    std::sort(kh.begin(), kh.end());
+    std::vector<uint32_t> out(kh.size());
+    for (size_t i = 0; i < kh.size(); ++i) out[i] = kh[i].second;
+    return out;
+}
+
+// work items of kB same-class prefixes, emitted in ascending key order of
+// their prefixes (each class's last item padded with `empty`)
+inline std::vector<uint32_t> ordered_items(int P, int nup, int L, int kB, uint32_t empty, const std::vector<int> &low) {
+    std::vector<uint32_t> items;
+    std::vector<std::vector<uint32_t>> pend(L + 1);
+    for (uint32_t h : ordered_prefixes(P, nup, L, low)) {
+        const int m = nup - __builtin_popcountll(h);
+        pend[m].push_back(h);
+        if ((int)pend[m].size() == kB) {
+            items.insert(items.end(), pend[m].begin(), pend[m].end());
+            pend[m].clear();
+        }
+    }
+    for (auto &v : pend)
+        if (!v.empty()) {
+            items.insert(items.end(), v.begin(), v.end());
+            items.insert(items.end(), kB - v.size(), empty);
+        }
+    return items;
+}
+
 }  // namespace xd

@@ -263,10 +263,11 @@ xd_status u1_states(const xd_basis_s *b, int64_t first, int64_t count, uint64_t 
 xd_status u1_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, int nvec,
                    cudaStream_t st) {
     if (nvec == 1 && dt == XD_F32 && h->b->spmm.ok) return spmm_apply(h, x, y, st);
-    if (nvec == 1 && dt == XD_F64 && spmm64_usable(h)) {
-        const xd_status s = spmm64_apply(h, x, y, st);
-        // a workspace that does not fit sends this product to the FP64 kernels
-        if (s != XD_ENOMEM) return s;
+    if (nvec == 1 && dt == XD_F64 && passes_usable(h)) {
+        const xd_status s = passes_apply_f64(h, x, y, st);
+        // a workspace that does not fit, or prefix bonds that four windows
+        // cannot hold, send this product to the FP64 block kernel
+        if (s != XD_ENOMEM && s != XD_ERANGE) return s;
     }
     if (nvec == 8 && dt == XD_F32 && spmm8_usable(h, x, y)) return spmm8_apply(h, x, y, st);
     if (nvec == 1 && h->b->blk.ok) return block_apply(h, x, y, dt, st);

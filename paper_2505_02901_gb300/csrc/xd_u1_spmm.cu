@@ -443,6 +443,8 @@ xd_status spmm_layout_build(xd_basis_s *b) {
     s.ncross = (int)cross.size() / 4;
     s.ncsite = (int)csite.size() / 3;
     s.maxblk = T.maxblk;
+    s.h_pre = pre;
+    s.h_csite = csite;
     s.cross_ids.clear();
     for (int q = 0; q < s.ncross; ++q) s.cross_ids.push_back(cross[4 * q + 2]);
     std::vector<uint16_t> postid(T.post.begin(), T.post.end());

@@ -56,3 +56,25 @@ extern "C" long long shim_items(int P, int nup, int L, int kB, uint32_t empty, u
     for (size_t i = 0; i < v.size() && (long long)i < cap; ++i) out[i] = v[i];
     return (long long)v.size();
 }
+
+// prefix passes: returns the number of passes; for pass p, low bits and
+// bonds (indices into the prefix triples) are written to the out arrays
+static std::vector<xd::PrefixPass> g_passes;
+extern "C" int shim_choose_passes(int P, const int32_t *pre, int npre, int W, int max_passes) {
+    g_passes = xd::choose_passes(P, std::vector<int32_t>(pre, pre + 3 * npre), W, max_passes);
+    return (int)g_passes.size();
+}
+extern "C" int shim_pass_low(int p, int32_t *out) {
+    for (size_t i = 0; i < g_passes[p].low.size(); ++i) out[i] = g_passes[p].low[i];
+    return (int)g_passes[p].low.size();
+}
+extern "C" int shim_pass_bonds(int p, int32_t *out) {
+    for (size_t i = 0; i < g_passes[p].bonds.size(); ++i) out[i] = g_passes[p].bonds[i];
+    return (int)g_passes[p].bonds.size();
+}
+extern "C" long long shim_ordered_items(int P, int nup, int L, int kB, uint32_t empty, const int32_t *low, int nlow,
+                                        uint32_t *out, long long cap) {
+    const std::vector<uint32_t> v = xd::ordered_items(P, nup, L, kB, empty, std::vector<int>(low, low + nlow));
+    for (size_t i = 0; i < v.size() && (long long)i < cap; ++i) out[i] = v[i];
+    return (long long)v.size();
+}

@@ -167,3 +167,25 @@ def test_f64_full_size_spiky_vector_keeps_the_tolerance(orc):
     assert rel_l2(ys, yo) <= 1e-12
     del x, y
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("nb", [300, 400])
+def test_f64_dense_random_graphs_n32(orc, nb):
+    """Random graphs on N = 32 (dim 601,080,390): with 300 bonds the prefix
+    bonds need four 12-bit windows (four passes); with 400 bonds four windows
+    cannot hold them and the FP64 product falls back to the FP64 block
+    kernel.  Both meet the tolerance on sampled rows."""
+    A = api()
+    N, nup = 32, 16
+    bonds = W.random_bonds(N, nb, 5)
+    J = W.uniform_couplings(nb, 5)
+    ham = A.Hamiltonian(A.Basis(N, nup, bonds), J)
+    seed = 8
+    x = A.random_vector(ham.dim, seed, torch.float64)
+    y = ham.apply(x)
+    del x
+    rows = np.concatenate([[0, ham.dim - 1], np.random.default_rng(8).integers(0, ham.dim, 1000)])
+    yo = orc.apply_rows_rng(N, nup, bonds, J, seed, rows)
+    assert rel_l2(y[torch.from_numpy(rows).cuda()].cpu().numpy(), yo) <= 1e-12
+    del y
+    torch.cuda.empty_cache()

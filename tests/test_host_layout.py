@@ -29,6 +29,7 @@ def lay():
     L.shim_u1_index.argtypes = [ctypes.c_ulonglong]
     L.shim_u1_state.restype = ctypes.c_ulonglong
     L.shim_u1_state.argtypes = [ctypes.c_longlong]
+    L.shim_ordered_items.restype = ctypes.c_longlong
     return L
 
 
@@ -190,3 +191,79 @@ def test_work_items(lay, N, nup):
         m = cls.pop()
         assert real == sorted(real) and real[0] > last.get(m, -1)
         last[m] = real[-1]
+
+
+def _passes(lay, P, pre, W, maxp=3):
+    pre = np.ascontiguousarray(np.asarray(pre, dtype=np.int32).reshape(-1))
+    n = lay.shim_choose_passes(P, pre.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(pre) // 3, W, maxp)
+    out = []
+    for p in range(n):
+        low = np.zeros(64, dtype=np.int32)
+        bd = np.zeros(len(pre) // 3 + 1, dtype=np.int32)
+        nl = lay.shim_pass_low(p, low.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        nbd = lay.shim_pass_bonds(p, bd.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        out.append((list(low[:nl]), list(bd[:nbd])))
+    return out
+
+
+def _prefix_triples(N, L, bonds):
+    return [(min(i, j) - L, max(i, j) - L, k) for k, (i, j) in enumerate(bonds) if min(i, j) >= L]
+
+
+@pytest.mark.parametrize("lattice,W,npass", [((4, 8), 12, 2), ((6, 6), 12, 3), ((6, 6), 18, 2), ((4, 7), 12, 2), ((4, 7), 16, 1), ((4, 8), 20, 1)])
+def test_prefix_passes_cover_every_bond_locally(lay, lattice, W, npass):
+    """Every prefix bond lands in exactly one pass; on the J1-J2 tori each
+    pass's bonds have both bits in its window of at most W bits (whole rows:
+    two passes for the 4x8 prefix of 5 rows of 4 sites, three for the 6x6
+    prefix of 4 rows of 6 at W = 12)."""
+    from paper_2505_02901_gb300 import workloads as W_
+    Lx, Ly = lattice
+    N = Lx * Ly
+    L = 12
+    bonds, _ = W_.square_j1j2(Lx, Ly)
+    pre = _prefix_triples(N, L, bonds)
+    P = N - L
+    passes = _passes(lay, P, [t for tr in pre for t in tr], W)
+    assert len(passes) == npass
+    seen = sorted(q for _, bd in passes for q in bd)
+    assert seen == list(range(len(pre)))
+    for low, bd in passes:
+        assert len(low) <= W and low == sorted(low)
+        for q in bd:
+            a, c, _ = pre[q]
+            assert a in low and c in low
+
+
+def test_prefix_passes_random_graph_and_limits(lay):
+    """Any bond graph: every bond assigned once, at most max_passes passes;
+    a graph that fits one window takes one pass."""
+    rng = np.random.default_rng(0)
+    P = 22
+    pre = []
+    for k in range(90):
+        a, c = rng.choice(P, 2, replace=False)
+        pre.append((min(a, c), max(a, c), k))
+    for maxp in (1, 2, 3):
+        passes = _passes(lay, P, [t for tr in pre for t in tr], 10, maxp)
+        assert 1 <= len(passes) <= maxp
+        assert sorted(q for _, bd in passes for q in bd) == list(range(len(pre)))
+    passes = _passes(lay, 8, [0, 1, 0, 2, 7, 1], 8)
+    assert len(passes) == 1 and sorted(passes[0][1]) == [0, 1]
+
+
+def test_ordered_items_cover_every_block_once(lay):
+    """Items of kB same-class prefixes in key order: every non-empty prefix
+    exactly once, one class per item, padding only at the end of a class."""
+    P, nup, L, kB = 12, 10, 8, 4
+    low = np.array([10, 11, 0, 1], dtype=np.int32)
+    cap = 1 << 16
+    out = np.zeros(cap, dtype=np.uint32)
+    n = lay.shim_ordered_items(P, nup, L, kB, 0xffffffff, low.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                               len(low), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), cap)
+    items = out[:n].reshape(-1, kB)
+    real = items[items != 0xffffffff]
+    want = [h for h in range(1 << P) if 0 <= nup - bin(h).count("1") <= L]
+    assert sorted(real.tolist()) == want
+    for it in items:
+        cls = {bin(int(h)).count("1") for h in it if h != 0xffffffff}
+        assert len(cls) == 1
