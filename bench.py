@@ -45,12 +45,17 @@ FORM_NOTE = {
 # dram__bytes_read.sum + dram__bytes_write.sum of one product launch at this
 # workload (ncu, profiles/apply_4x8_*.md); None until measured for the
 # kernel as it stands
-TRAFFIC = {"f32": 71.64e9, "f64": None}
-# the kernel each form's product runs at this workload
-KERNEL = {"f32": "k_spmm<12>", "f64": "k_spmm64<PolFX> (+ k_x64_stats, k_x64_convert)"}
+# FP64: the sum over the product's kernels, captured at 4x7 (the 4x8 workload
+# holds too much device memory for a multi-pass capture) and scaled to 4x8
+# by rows (profiles/apply64_4x7_passes_full.md)
+TRAFFIC = {"f32": 71.64e9, "f64": 3.5e9 * 601080390 / 40116600}
+# the kernels each form's product runs at this workload
+KERNEL = {"f32": "k_spmm<12>",
+          "f64": "k_x64_stats, k_x64_convert, 2 x k_tpass<PolFX>, k_main<PolFX, 4> (dominant, 56%)"}
 # kernels of this library launched per product (FP64: statistics, conversion,
-# the fixed-point product and the double-float product, which returns at once)
-LAUNCHES = {"f32": 1, "f64": 4}
+# the fixed-point passes and main kernel, and their double-float instances,
+# which return at once)
+LAUNCHES = {"f32": 1, "f64": 8}
 # GB300 HBM3e nominal bandwidth (the measured copy bandwidth is the peak used)
 HBM_NOMINAL_GBS = 7900.0
 
@@ -783,7 +788,10 @@ def main():
                      "kernel": KERNEL[head], "peak_kind": peak_kind,
                      "frac_of_nominal": fh["hbm_gbs_compulsory"] / HBM_NOMINAL_GBS,
                      "nominal_peak": HBM_NOMINAL_GBS,
-                     "note": f"achieved = compulsory 2*{esize}*dim bytes per H.v / mean launch time"},
+                     "note": (f"achieved = compulsory 2*{esize}*dim bytes per H.v / mean CUDA-event time of the "
+                              "whole product call (all its kernels); traffic = DRAM bytes of one product "
+                              + ("(sum over its kernels, 4x7 capture scaled by rows)" if head == "f64" else
+                                 "(one k_spmm launch, full-size capture)"))},
         "forms": forms,
         "clocks": clk.summary(),
         "e2e": {"value": whole_job_rate(world, elements, e2e_ms), "unit": "elements/s",
