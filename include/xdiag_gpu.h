@@ -146,6 +146,17 @@ xd_status xd_apply(xd_ham h, const void *x, void *y, xd_dtype dtype,
 xd_status xd_apply_bilinear(xd_ham h, const void *g, const void *x,
                             xd_dtype dtype, double *dJ, xd_stream stream);
 
+/* Per-bond bilinear forms summed over nvec columns: dJ[b] = sum_k Re <g_k|
+ * S_{i_b}.S_{j_b} |x_k> for row-major [dim][nvec] device arrays g, x (the
+ * J_b-derivative of Re sum_k <g_k|H|x_k>, the backward of a product on a
+ * block of vectors; Sec. 3.7 inner, Sec. 5.1 multi-vector apply).  nvec in
+ * {1, 2, 4, 8}; nvec > 1 on U(1) blocks with XD_F64 or XD_F32.  dJ: device
+ * [nb] doubles.  Every column is reduced in a fixed order and the columns are
+ * summed in a fixed order (deterministic).  Asynchronous. */
+xd_status xd_apply_bilinear_nvec(xd_ham h, const void *g, const void *x,
+                                 xd_dtype dtype, int nvec, double *dJ,
+                                 xd_stream stream);
+
 /* Same per-bond bilinear forms as xd_apply_bilinear, for callers that must
  * not have the library allocate device memory: a process whose allocator
  * owns all of the GPU's memory (a pool or a fixed budget set at start-up),
@@ -168,15 +179,19 @@ xd_status xd_apply_bilinear(xd_ham h, const void *g, const void *x,
 xd_status xd_apply_bilinear_noalloc(xd_ham h, const void *g, const void *x,
                                     xd_dtype dtype, double *dJ, xd_stream stream);
 
-/* Two-point spin correlations of a state on a U(1) block (the expectation
- * values of Sec. 3.7 inner, with the SzSz / SdotS operators of App. A on
- * arbitrary site pairs): out[p] = <psi| O |psi> for pair p = (i_p, j_p),
- * O = Sz_i Sz_j (kind 0) or S_i.S_j (kind 1); i = j is allowed ((Sz_i)^2 =
- * 1/4, S_i.S_i = 3/4 times <psi|psi>).  psi is not normalised by the call.
- * psi: device [dim] vector of dtype XD_F64 or XD_F32; pairs: host
- * [npairs][2] site indices in [0, N); out: host [npairs] doubles.  Sums run
- * in FP64 in a fixed order (deterministic).  Symmetry-adapted blocks are
- * rejected (XD_EINVAL).  Synchronous; allocates its workspace per call. */
+/* Two-point spin correlations of a state (the expectation values of Sec. 3.7
+ * inner, with the SzSz / SdotS operators of App. A on arbitrary site pairs):
+ * out[p] = <psi| O |psi> for pair p = (i_p, j_p), O = Sz_i Sz_j (kind 0) or
+ * S_i.S_j (kind 1); i = j is allowed ((Sz_i)^2 = 1/4, S_i.S_i = 3/4 times
+ * <psi|psi>).  psi is not normalised by the call.  U(1) blocks: psi a device
+ * [dim] vector of XD_F64 or XD_F32.  Symmetry-adapted blocks (Sec. 3.10):
+ * psi of XD_F64 (real block) or XD_C128 (complex block), the value is that
+ * of the lifted state |psi> = sum_r psi_r |r_chi>; within a one-dimensional
+ * irrep it is the same on every pair of an orbit of the group, and the call
+ * forms it from the symmetric bond form of the pair's orbit on the block's
+ * own representatives.  pairs: host [npairs][2] site indices in [0, N); out:
+ * host [npairs] doubles.  Sums run in FP64 in a fixed order
+ * (deterministic).  Synchronous; allocates its workspace per call. */
 xd_status xd_correlations(xd_basis b, const void *psi, xd_dtype dtype,
                           const int32_t *pairs, int npairs, int kind,
                           double *out);
@@ -224,9 +239,12 @@ xd_status xd_evolve(xd_ham h, const void *psi0, double z_re, double z_im,
  * Jaklic-Prelovsek): R seeded random start vectors (start r is the
  * standard-normal vector of xd_random_vector with seed + r), each run
  * through M plain Lanczos steps (a run whose beta drops below 1e-13
- * max|alpha| stops early), eight at a time through the eight-vector product.
- * U(1) blocks.  Host outputs: alpha, beta [R][M] (zero past n_iter[r]),
- * n_iter [R].  Synchronous.  Device workspace: three [dim][8] FP64 arrays. */
+ * max|alpha| stops early).  U(1) blocks run eight starts at a time through
+ * the eight-vector product (device workspace: three [dim][8] FP64 arrays);
+ * symmetry-adapted blocks run one Lanczos pass per start on the block's own
+ * product (complex vectors on complex blocks; workspace: three vectors).
+ * Host outputs: alpha, beta [R][M] (zero past n_iter[r]), n_iter [R].
+ * Synchronous. */
 xd_status xd_ftlm(xd_ham h, int R, int M, uint64_t seed, double *alpha,
                   double *beta, int *n_iter);
 

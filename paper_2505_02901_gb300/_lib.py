@@ -46,6 +46,7 @@ SIGNATURES = {
     "xd_apply": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
     "xd_apply_bilinear": (_i, [_vp, _vp, _vp, _i, _vp, _vp]),
     "xd_apply_bilinear_noalloc": (_i, [_vp, _vp, _vp, _i, _vp, _vp]),
+    "xd_apply_bilinear_nvec": (_i, [_vp, _vp, _vp, _i, _i, _vp, _vp]),
     "xd_correlations": (_i, [_vp, _vp, _i, _c.POINTER(_c.c_int32), _i, _i, _dp]),
     "xd_evolve": (_i, [_vp, _vp, _c.c_double, _c.c_double, _i, _c.c_double, _vp, _c.POINTER(_i), _dp]),
     "xd_ftlm": (_i, [_vp, _i, _i, _u64, _dp, _dp, _c.POINTER(_i)]),

@@ -95,48 +95,18 @@ class Basis:
 
     def correlations(self, psi: torch.Tensor, pairs, kind: str = "ss") -> np.ndarray:
         """<psi| O_ij |psi> for every site pair, O = S_i.S_j (kind "ss") or
-        Sz_i Sz_j (kind "zz") (Sec. 3.7 inner).  U(1) blocks: both kinds.
-        Symmetry-adapted blocks: kind "ss", through the symmetric bond form
-        on the orbits of the pairs (psi normalised)."""
+        Sz_i Sz_j (kind "zz") (Sec. 3.7 inner), on U(1) and symmetry-adapted
+        blocks (the lifted state's values; xd_correlations)."""
         _check_vec(psi, self.dim, "psi")
+        if kind not in ("zz", "ss"):
+            raise XDError(XD_EINVAL, f"correlations: kind must be 'zz' or 'ss', not {kind!r}")
         p = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
-        if self.symmetric:
-            return self._orbit_correlations(psi, p, kind)
         out = np.zeros(p.shape[0])
         torch.cuda.current_stream().synchronize()
         check(_lib.lib().xd_correlations(self._h, _ptr(psi), _dtype_code(psi),
                                          p.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), p.shape[0],
                                          {"zz": 0, "ss": 1}[kind], out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out
-
-    def _orbit_correlations(self, psi, p, kind):
-        """Within a one-dimensional irrep <psi|S_i.S_j|psi> is the same on every
-        site pair of one orbit of the group (Sec. 3.10), which is what the
-        symmetric bond form returns per bond.  The pairs' orbits become the
-        bonds of an auxiliary block of the same group and irrep (the same
-        representatives, so psi is a vector of it) with unit couplings."""
-        if kind != "ss":
-            raise XDError(XD_EINVAL, "correlations: symmetry-adapted blocks give S_i.S_j only (kind 'ss')")
-        if p.size and (p.min() < 0 or p.max() >= self.N):
-            raise XDError(XD_EINVAL, f"correlations: site pairs must lie in 0..{self.N - 1}")
-        key = lambda i, j: (min(i, j), max(i, j))  # noqa: E731
-        bonds, where = [], {}
-        for i, j in p.tolist():
-            if i == j or key(i, j) in where:
-                continue
-            for g in self._perms:
-                e = key(int(g[i]), int(g[j]))
-                if e not in where:
-                    where[e] = len(bonds)
-                    bonds.append(e)
-        f = None
-        if bonds:
-            aux = Basis(self.N, self.nup, np.array(bonds, dtype=np.int32),
-                        symmetry=(self._perms, self._cr + 1j * self._ci))
-            if aux.dim != self.dim:
-                raise RuntimeError("auxiliary block of the pair orbits has another dimension")
-            f = Hamiltonian(aux, np.ones(len(bonds))).bilinear(psi, psi).cpu().numpy()
-        return np.array([0.75 if i == j else f[where[key(i, j)]] for i, j in p.tolist()])
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -174,13 +144,16 @@ class Hamiltonian:
         return y
 
     def bilinear(self, g: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
-        """dJ[b] = Re <g| S_i.S_j |x> for every bond (device float64 [nb])."""
+        """dJ[b] = Re <g| S_i.S_j |x> for every bond (device float64 [nb]);
+        for [dim, nvec] g and x, the sum over the columns."""
         _check_vec(g, self.dim, "g")
         _check_vec(x, self.dim, "x")
-        if g.dtype != x.dtype:
-            raise TypeError("g and x must have the same dtype")
+        if g.dtype != x.dtype or g.shape != x.shape:
+            raise TypeError("g and x must have the same dtype and shape")
+        nvec = 1 if x.dim() == 1 else x.shape[1]
         out = torch.empty(self.basis.nb, dtype=torch.float64, device=x.device)
-        check(_lib.lib().xd_apply_bilinear(self._h, _ptr(g), _ptr(x), _dtype_code(x), _ptr(out), _stream()))
+        check(_lib.lib().xd_apply_bilinear_nvec(self._h, _ptr(g), _ptr(x), _dtype_code(x), nvec, _ptr(out),
+                                                _stream()))
         return out
 
     def _lanczos(self, max_iter, seed, storage, nev, psi=None):
@@ -231,22 +204,14 @@ class Hamiltonian:
 
     def ftlm(self, R: int = 16, M: int = 80, seed: int = 1):
         """Finite-temperature Lanczos tridiagonals of R random starts (seed + r),
-        M steps each; returns (alpha [R, M], beta [R, M], n_iter [R]).  U(1)
-        blocks run eight starts at a time on the eight-vector product;
-        symmetry-adapted blocks run one Lanczos pass per start on their own
-        product (the same seeded starts)."""
+        M steps each; returns (alpha [R, M], beta [R, M], n_iter [R]) (xd_ftlm:
+        U(1) blocks eight starts at a time on the eight-vector product,
+        symmetry-adapted blocks one Lanczos pass per start)."""
         if R < 1 or M < 1:
             raise XDError(XD_EINVAL, "ftlm: need R >= 1 and M >= 1")
         a = np.zeros((R, M))
         b = np.zeros((R, M))
         n = np.zeros(R, dtype=np.int32)
-        if self.basis.symmetric:
-            storage = torch.complex128 if self.basis.is_complex else torch.float64
-            for r in range(R):
-                info = self._lanczos(M, seed + r, storage, 1)
-                k = info["n_iter"]
-                a[r, :k], b[r, :k], n[r] = info["alpha"], info["beta"], k
-            return a, b, n
         torch.cuda.current_stream().synchronize()
         dp = ctypes.POINTER(ctypes.c_double)
         check(_lib.lib().xd_ftlm(self._h, int(R), int(M), ctypes.c_uint64(seed), a.ctypes.data_as(dp),
@@ -319,6 +284,7 @@ class HeisenbergApply(torch.autograd.Function):
         if not np.array_equal(Jn, ham.J):
             ham.set_couplings(Jn)
         ctx.ham = ham
+        ctx.jdev = J.device
         ctx.save_for_backward(x)
         return ham.apply(x.contiguous())
 
@@ -328,12 +294,7 @@ class HeisenbergApply(torch.autograd.Function):
         ham = ctx.ham
         g = g.contiguous()
         gx = ham.apply(g) if ctx.needs_input_grad[1] else None
-        gJ = None
-        if ctx.needs_input_grad[0]:
-            if x.dim() == 1:
-                gJ = ham.bilinear(g, x.contiguous()).to(torch.float64)
-            else:
-                gJ = sum(ham.bilinear(g[:, k].contiguous(), x[:, k].contiguous()) for k in range(x.shape[1]))
+        gJ = ham.bilinear(g, x.contiguous()).to(ctx.jdev) if ctx.needs_input_grad[0] else None
         return gJ, gx, None
 
 

@@ -585,6 +585,17 @@ xd_status xd_apply_bilinear(xd_ham h, const void *g, const void *x, xd_dtype dt,
     return u1_bilinear(h, g, x, dt, dJ, (cudaStream_t)stream);
 }
 
+xd_status xd_apply_bilinear_nvec(xd_ham h, const void *g, const void *x, xd_dtype dt, int nvec, double *dJ,
+                                 xd_stream stream) {
+    if (!dJ || !h || !g || !x) {
+        set_error("xd_apply_bilinear_nvec: NULL argument");
+        return XD_EINVAL;
+    }
+    XD_TRY(check_vec_args(h, g, x, dt, nvec, "xd_apply_bilinear_nvec", true));
+    if (nvec == 1) return xd_apply_bilinear(h, g, x, dt, dJ, stream);
+    return u1_bilinear_nvec(h, g, x, dt, nvec, dJ, (cudaStream_t)stream);
+}
+
 xd_status xd_random_vector(int64_t dim, uint64_t seed, void *out, xd_dtype dt,
                            xd_stream stream) {
     if (!out || dim < 0) {

@@ -214,6 +214,8 @@ xd_status u1_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt,
 xd_status u1_bilinear(const xd_ham_s *h, const void *g, const void *x,
                       xd_dtype dt, double *dJ, cudaStream_t st);
 xd_status u1_states(const xd_basis_s *b, int64_t first, int64_t count, uint64_t *out, cudaStream_t st);
+xd_status u1_bilinear_nvec(const xd_ham_s *h, const void *g, const void *x, xd_dtype dt, int nv, double *dJ,
+                           cudaStream_t st);
 // symmetric blocks (xd_sym.cu)
 xd_status sym_build(xd_basis_s *b);
 xd_status sym_ham_tables(xd_ham_s *h);
@@ -221,6 +223,8 @@ xd_status sym_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt,
                     cudaStream_t st);
 xd_status sym_bilinear(const xd_ham_s *h, const void *g, const void *x,
                        xd_dtype dt, double *dJ, cudaStream_t st);
+xd_status sym_correlations(const xd_basis_s *b, const void *psi, xd_dtype dt, const int32_t *pairs, int npairs,
+                           int kind, double *out);
 // vector kernels (xd_vec.cu)
 xd_status vec_random(int64_t n, uint64_t seed, void *out, xd_dtype dt,
                      cudaStream_t st);

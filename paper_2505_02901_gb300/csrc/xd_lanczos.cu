@@ -579,15 +579,23 @@ xd_status xd_ftlm(xd_ham h, int R, int M, uint64_t seed, double *alpha, double *
         set_error("xd_ftlm: NULL argument");
         return XD_EINVAL;
     }
-    if (h->b->sym) {
-        set_error("xd_ftlm: U(1) blocks only (the eight-vector product)");
-        return XD_EINVAL;
-    }
     if (R < 1 || R > (1 << 16) || M < 1 || M > 2000) {
         set_error("xd_ftlm: R = %d or M = %d out of range", R, M);
         return XD_EINVAL;
     }
     for (size_t q = 0; q < (size_t)R * M; ++q) alpha[q] = beta[q] = 0.0;
+    if (h->b->sym) {
+        // symmetry-adapted blocks: one Lanczos pass per start on the block's
+        // own product (complex vectors on complex blocks), same seeded starts
+        const xd_dtype dt = h->b->cplx ? XD_C128 : XD_F64;
+        for (int r = 0; r < R; ++r) {
+            int n = 0;
+            XD_TRY(lanczos_run<double>(h, M, seed + (uint64_t)r, dt, alpha + (size_t)r * M, beta + (size_t)r * M, &n,
+                                       nullptr, nullptr));
+            n_iter[r] = n;
+        }
+        return XD_OK;
+    }
     return ftlm_run(h, R, M, seed, alpha, beta, n_iter);
 }
 

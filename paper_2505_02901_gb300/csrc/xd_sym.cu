@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <string>
 #include <unordered_map>
 
@@ -462,7 +463,7 @@ __global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, const double 
 // reduced per CTA into part[cta][b] (fixed order).
 constexpr int kChunk = 128;
 
-template <bool CPLX>
+template <bool CPLX, bool ZZ = false>
 __global__ void __launch_bounds__(kThreads) k_sym_bilinear(SymView v, const uint64_t *__restrict__ masks,
                                                            int nb, int b0, const double *__restrict__ chi,
                                                            const double *__restrict__ sq,
@@ -499,7 +500,7 @@ __global__ void __launch_bounds__(kThreads) k_sym_bilinear(SymView v, const uint
                 // Re conj(g_r) * (term) ; diagonal term is +-1/4 x_r
                 const double diag = (t == 0 || t == mk) ? 0.25 : -0.25;
                 val = diag * (gr * xr + gi * xi);
-                if (!(t == 0 || t == mk)) {
+                if (!ZZ && !(t == 0 || t == mk)) {
                     const Orbit o = orbit_min(v, s ^ mk);
                     const int64_t k = __ldg(v.u1.hi_off + (o.rep >> v.u1.L)) +
                                       (int64_t)__ldg(v.u1.lo_rank + (o.rep & v.u1.lomask));
@@ -738,6 +739,84 @@ xd_status sym_bilinear(const xd_ham_s *h, const void *g, const void *x, xd_dtype
     }
     k_orbit_mean<<<(nb + 127) / 128, 128, 0, st>>>(w.part, grid, nb, w.orbit, dJ);
     XD_CUDA(cudaGetLastError());
+    return XD_OK;
+}
+
+// Two-point correlations on a symmetry-adapted block: the pairs' orbits under
+// the group become a list of site pairs (each unordered pair once) with an
+// orbit id; the symmetric bond form of every listed pair (its diagonal part
+// alone for Sz Sz) is averaged over its orbit, which is <psi| O_ij |psi> of
+// the lifted state for every pair of the orbit (within a one-dimensional
+// irrep the expectation value is constant on a pair orbit, Sec. 3.10).
+xd_status sym_correlations(const xd_basis_s *b, const void *psi, xd_dtype dt, const int32_t *pairs, int npairs,
+                           int kind, double *out) {
+    const int N = b->N, G = b->G;
+    std::vector<uint64_t> masks;
+    std::vector<int32_t> orb;
+    std::map<std::pair<int, int>, int> where;
+    std::vector<int> slot(npairs);
+    int norb = 0;
+    for (int q = 0; q < npairs; ++q) {
+        const int i = std::min(pairs[2 * q], pairs[2 * q + 1]), j = std::max(pairs[2 * q], pairs[2 * q + 1]);
+        auto it = where.find({i, j});
+        if (it == where.end()) {
+            for (int g = 0; g < G; ++g) {
+                const int32_t *pg = b->perms.data() + (size_t)g * N;
+                const std::pair<int, int> e(std::min(pg[i], pg[j]), std::max(pg[i], pg[j]));
+                if (where.count(e)) continue;
+                where[e] = (int)masks.size();
+                masks.push_back((1ull << e.first) | (1ull << e.second));
+                orb.push_back(norb);
+            }
+            ++norb;
+            it = where.find({i, j});
+        }
+        slot[q] = it->second;
+    }
+    const int nm = (int)masks.size();
+    const SymView v = b->symview();
+    const int grid = grid_for(v.dim, kThreads, 4);
+    std::vector<double> sq(2 * (size_t)(G + 1), 0.0);
+    for (int a = 1; a <= G; ++a) {
+        sq[a] = sqrt((double)a);
+        sq[G + 1 + a] = 1.0 / sqrt((double)a);
+    }
+    uint64_t *d_m = nullptr;
+    int32_t *d_o = nullptr;
+    double *d_sq = nullptr, *d_part = nullptr, *d_out = nullptr;
+    cudaError_t e = dev_malloc((void **)&d_m, sizeof(uint64_t) * nm);
+    if (e == cudaSuccess) e = dev_malloc((void **)&d_o, sizeof(int32_t) * nm);
+    if (e == cudaSuccess) e = dev_malloc((void **)&d_sq, sizeof(double) * sq.size());
+    if (e == cudaSuccess) e = dev_malloc((void **)&d_part, sizeof(double) * (size_t)grid * nm);
+    if (e == cudaSuccess) e = dev_malloc((void **)&d_out, sizeof(double) * nm);
+    if (e == cudaSuccess) e = cudaMemcpy(d_m, masks.data(), sizeof(uint64_t) * nm, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_o, orb.data(), sizeof(int32_t) * nm, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_sq, sq.data(), sizeof(double) * sq.size(), cudaMemcpyHostToDevice);
+    for (int b0 = 0; e == cudaSuccess && b0 < nm; b0 += kChunk) {
+        if (dt == XD_C128) {
+            if (kind) k_sym_bilinear<true, false><<<grid, kThreads>>>(v, d_m, nm, b0, b->d_chi, d_sq, (const double2 *)psi, (const double2 *)psi, d_part);
+            else k_sym_bilinear<true, true><<<grid, kThreads>>>(v, d_m, nm, b0, b->d_chi, d_sq, (const double2 *)psi, (const double2 *)psi, d_part);
+        } else {
+            if (kind) k_sym_bilinear<false, false><<<grid, kThreads>>>(v, d_m, nm, b0, b->d_chi, d_sq, (const double *)psi, (const double *)psi, d_part);
+            else k_sym_bilinear<false, true><<<grid, kThreads>>>(v, d_m, nm, b0, b->d_chi, d_sq, (const double *)psi, (const double *)psi, d_part);
+        }
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        k_orbit_mean<<<(nm + 127) / 128, 128>>>(d_part, grid, nm, d_o, d_out);
+        e = cudaGetLastError();
+    }
+    std::vector<double> val(nm, 0.0);
+    if (e == cudaSuccess) e = cudaMemcpy(val.data(), d_out, sizeof(double) * nm, cudaMemcpyDeviceToHost);
+    cudaFree(d_m);
+    cudaFree(d_o);
+    cudaFree(d_sq);
+    cudaFree(d_part);
+    cudaFree(d_out);
+    if (e != cudaSuccess) return cuda_status(e, "xd_correlations (symmetric block)");
+    // a pair i = j has a one-bit mask that never flips: <psi|psi>/4 = (Sz_i)^2;
+    // S_i.S_i = 3/4 <psi|psi> is three times that
+    for (int q = 0; q < npairs; ++q) out[q] = val[slot[q]] * ((kind && pairs[2 * q] == pairs[2 * q + 1]) ? 3.0 : 1.0);
     return XD_OK;
 }
 

@@ -160,7 +160,8 @@ template <typename T, int MBW, bool ZZ>
 __global__ void __launch_bounds__(kBT) k_bilinear_bp(U1View u, const uint64_t *__restrict__ masks,
                                                      int nb, int b0, const T *__restrict__ g,
                                                      const T *__restrict__ x,
-                                                     double *__restrict__ part) {
+                                                     double *__restrict__ part, int nv) {
+    // nv > 1: column of row-major [dim][nv] vectors (g, x point at the column)
     __shared__ uint64_t sh_s[kBT];
     __shared__ double sh_g[kBT], sh_p[kBT];
     __shared__ double sh_red[kBT / 32];
@@ -180,8 +181,8 @@ __global__ void __launch_bounds__(kBT) k_bilinear_bp(U1View u, const uint64_t *_
     for (int64_t base = (int64_t)blockIdx.x * kBT; base < u.dim; base += (int64_t)gridDim.x * kBT) {
         const int64_t r = base + tid;
         const RowState rs = unrank_tile(u, base, r, sh_range);
-        const double gr = rs.valid ? (double)g[r] : 0.0;
-        const double pr = rs.valid ? gr * (double)x[r] : 0.0;
+        const double gr = rs.valid ? (double)g[r * nv] : 0.0;
+        const double pr = rs.valid ? gr * (double)x[r * nv] : 0.0;
         P += pr;
         sh_s[tid] = rs.s;
         sh_g[tid] = gr;
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(kBT) k_bilinear_bp(U1View u, const uint64_t *_
                 if (tb != 0 && tb != mk[j]) {
                     if (!ZZ) {
                         const int64_t c = rank_of(u, s ^ mk[j]);
-                        F[j] = fma(gq, (double)__ldg(x + c), F[j]);
+                        F[j] = fma(gq, (double)__ldg(x + c * nv), F[j]);
                     }
                     Fd[j] += pq;
                 }
@@ -289,12 +290,12 @@ xd_status u1_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, int n
 
 template <typename T, bool ZZ = false>
 static xd_status launch_bilinear_bp(const U1View &u, const uint64_t *masks, int nb, int grid, const void *g,
-                                    const void *x, double *part, cudaStream_t st) {
+                                    const void *x, double *part, cudaStream_t st, int nv = 1) {
     for (int b0 = 0; b0 < nb; b0 += kChunk) {
         const int nbc = std::min(kChunk, nb - b0);
         const int mbw = (nbc + 31) / 32;
         auto go = [&](auto kern) {
-            kern<<<grid, kBT, 0, st>>>(u, masks, nb, b0, (const T *)g, (const T *)x, part);
+            kern<<<grid, kBT, 0, st>>>(u, masks, nb, b0, (const T *)g, (const T *)x, part, nv);
         };
         if (mbw <= 1) go(k_bilinear_bp<T, 1, ZZ>);
         else if (mbw <= 2) go(k_bilinear_bp<T, 2, ZZ>);
@@ -302,6 +303,30 @@ static xd_status launch_bilinear_bp(const U1View &u, const uint64_t *masks, int 
         else go(k_bilinear_bp<T, 8, ZZ>);
         XD_CUDA(cudaGetLastError());
     }
+    return XD_OK;
+}
+
+// dJ[b] = sum over the nv columns of the per-bond forms: the partials of
+// column k fill rows [k grid, (k + 1) grid) and one fixed-order sum over all
+// rows follows (deterministic).
+xd_status u1_bilinear_nvec(const xd_ham_s *h, const void *g, const void *x, xd_dtype dt, int nv, double *dJ,
+                           cudaStream_t st) {
+    const xd_basis_s *b = h->b;
+    const int nb = b->nb;
+    const U1View u = b->u1view();
+    const int grid = grid_for(u.dim, kBT, 1);
+    xd_ham_s *hm = const_cast<xd_ham_s *>(h);
+    XD_TRY(ensure_partials(hm, sizeof(double) * (size_t)grid * nb * nv));
+    const uint64_t *d_masks = (const uint64_t *)(h->d_bond + nb);
+    const size_t es = dt == XD_F64 ? sizeof(double) : sizeof(float);
+    for (int k = 0; k < nv; ++k) {
+        const void *gk = (const char *)g + k * es, *xk = (const char *)x + k * es;
+        double *pk = hm->d_part + (size_t)k * grid * nb;
+        if (dt == XD_F64) XD_TRY(launch_bilinear_bp<double>(u, d_masks, nb, grid, gk, xk, pk, st, nv));
+        else XD_TRY(launch_bilinear_bp<float>(u, d_masks, nb, grid, gk, xk, pk, st, nv));
+    }
+    k_sum_columns<<<(nb + 127) / 128, 128, 0, st>>>(hm->d_part, grid * nv, nb, dJ);
+    XD_CUDA(cudaGetLastError());
     return XD_OK;
 }
 
@@ -422,12 +447,9 @@ extern "C" xd_status xd_correlations(xd_basis b, const void *psi, xd_dtype dt, c
         set_error("xd_correlations: NULL argument");
         return XD_EINVAL;
     }
-    if (b->sym) {
-        set_error("xd_correlations: U(1) blocks only (this block is symmetry-adapted)");
-        return XD_EINVAL;
-    }
-    if (dt != XD_F64 && dt != XD_F32) {
-        set_error("xd_correlations: dtype must be XD_F64 or XD_F32");
+    if (b->sym ? dt != (b->cplx ? XD_C128 : XD_F64) : (dt != XD_F64 && dt != XD_F32)) {
+        set_error(b->sym ? "xd_correlations: a symmetric block takes XD_F64 (real) or XD_C128 (complex)"
+                         : "xd_correlations: dtype must be XD_F64 or XD_F32");
         return XD_EINVAL;
     }
     if (kind != 0 && kind != 1) {
@@ -452,6 +474,7 @@ extern "C" xd_status xd_correlations(xd_basis b, const void *psi, xd_dtype dt, c
         for (int q = 0; q < npairs; ++q) out[q] = 0.0;
         return XD_OK;
     }
+    if (b->sym) return sym_correlations(b, psi, dt, pairs, npairs, kind, out);
     const U1View u = b->u1view();
     const int grid = grid_for(u.dim, kBT, 1);
     uint64_t *d_m = nullptr;

@@ -54,11 +54,14 @@ def test_correlations_errors():
         basis.correlations(psi, [(0, 8)])
     with pytest.raises(A.XDError):
         basis.correlations(psi.to(torch.complex128), [(0, 1)])
-    # symmetry-adapted blocks: S_i.S_j only, pairs inside the lattice
+    # symmetry-adapted blocks: pairs inside the lattice, the block's own dtype
     sym = A.Basis(8, 4, W.chain(8), symmetry=(W.chain_translations(8), W.chain_characters(8, 0)))
     zero = torch.zeros(sym.dim, dtype=torch.float64, device="cuda")
-    with pytest.raises(A.XDError):
-        sym.correlations(zero, [(0, 1)], "zz")
+    assert np.all(sym.correlations(zero, [(0, 1), (2, 2)], "zz") == 0.0)
     with pytest.raises(A.XDError):
         sym.correlations(zero, [(0, 8)])
+    with pytest.raises(A.XDError):
+        sym.correlations(zero.to(torch.complex128), [(0, 1)])
+    with pytest.raises(A.XDError):
+        sym.correlations(zero, [(0, 1)], "xx")
 

@@ -125,3 +125,49 @@ def test_energy_gradient_ladder(orc):
         assert abs(fd - g[b]) < 1e-6
     assert abs(J @ g - w[0]) < 1e-9
     assert np.abs(g[2 * L:3 * L] - g[3 * L:]).max() < 1e-9
+
+
+def test_bilinear_columns_and_autograd_block(orc):
+    """xd_apply_bilinear_nvec: the per-bond forms summed over the columns of
+    [dim][nvec] g and x equal the sum of the single-column forms (FP64 and
+    FP32; a small block and one on the FP32 batched layout), and the backward
+    of a product on a block of vectors gives that sum."""
+    A = api()
+    for N, nup, bonds, J in [(14, 7, W.ladder(7, 2), W.uniform_couplings(28, 5)),
+                             (24, 12, W.random_bonds(24, 40, 6), W.uniform_couplings(40, 6))]:
+        ham = A.Hamiltonian(A.Basis(N, nup, bonds), J)
+        for dt, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+            for nvec in (2, 4, 8):
+                g = torch.stack([A.random_vector(ham.dim, 10 + k, dt) for k in range(nvec)], 1).contiguous()
+                x = torch.stack([A.random_vector(ham.dim, 30 + k, dt) for k in range(nvec)], 1).contiguous()
+                got = ham.bilinear(g, x).cpu().numpy()
+                want = sum(ham.bilinear(g[:, k].contiguous(), x[:, k].contiguous()).cpu().numpy()
+                           for k in range(nvec))
+                assert np.abs(got - want).max() <= tol * np.abs(want).max()
+    ham = A.Hamiltonian(A.Basis(14, 7, W.ladder(7, 2)), W.uniform_couplings(28, 5))
+    Jt = torch.tensor(ham.J, requires_grad=True)
+    x = torch.stack([A.random_vector(ham.dim, 50 + k, torch.float64) for k in range(4)], 1).contiguous()
+    y = A.heisenberg_apply(ham, Jt, x)
+    w = torch.stack([A.random_vector(ham.dim, 70 + k, torch.float64) for k in range(4)], 1).contiguous()
+    (y * w).sum().backward()
+    want = ham.bilinear(w, x).cpu().numpy()
+    assert np.abs(Jt.grad.numpy() - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_basis_states_u1_and_range_errors(orc):
+    """xd_basis_states on U(1) blocks: the words of a row range equal the
+    oracle's enumeration (first, last and random ranges, int64 rows at N = 36
+    through the counting index); ranges outside the block are XD_ERANGE."""
+    A = api()
+    st = orc.enumerate_states(16, 8)
+    basis = A.Basis(16, 8, W.chain(16))
+    assert np.array_equal(basis.states().cpu().numpy().astype(np.uint64), st)
+    assert np.array_equal(basis.states(100, 37).cpu().numpy().astype(np.uint64), st[100:137])
+    big = A.Basis(36, 18, W.chain(36))
+    for first in (0, big.dim - 5, 2**32 - 2, 123456789):
+        w = big.states(first, 5).cpu().numpy()
+        assert [int(v) for v in w] == [orc.state_count(36, 18, first + k) for k in range(5)]
+    from paper_2505_02901_gb300._lib import XD_ERANGE, XDError
+    with pytest.raises(XDError) as e:
+        basis.states(basis.dim - 2, 5)
+    assert e.value.status == XD_ERANGE

@@ -26,23 +26,27 @@ def _sym_case(case):
 
 @pytest.mark.parametrize("case", range(3))
 def test_symmetric_block_correlations(orc, case):
-    """<psi|S_i.S_j|psi> on symmetry-adapted blocks (the symmetric bond form
-    on the orbits of the pairs) against the oracle's U(1) correlations of the
-    lifted state, for the block's lowest state."""
+    """<psi|S_i.S_j|psi> and <psi|Sz_i Sz_j|psi> on symmetry-adapted blocks
+    (through xd_correlations: the symmetric bond form on the orbits of the
+    pairs, on the block's own representatives) against the oracle's U(1)
+    correlations of the lifted state: the block's lowest state, and the same
+    state scaled by 2.5 (values, i = j included, scale with <psi|psi>)."""
     A = api()
     N, nup, bonds, J, perms, chi = _sym_case(case)
     basis = A.Basis(N, nup, bonds, symmetry=(perms, chi))
     ham = A.Hamiltonian(basis, J)
     storage = torch.complex128 if basis.is_complex else torch.float64
     _, psi, _ = ham.ground_state(max_iter=120, seed=2, storage=storage)
-    pairs = [(0, j) for j in range(N)] + [(3, 7), (5, 5), (N - 1, 2)]
-    got = basis.correlations(psi, pairs)
+    pairs = [(0, j) for j in range(N)] + [(3, 7), (5, 5), (N - 1, 2), (7, 3)]
     st = orc.enumerate_states(N, nup)
-    v = orc.SymBlock(N, nup, perms, chi).lift(st) @ psi.cpu().numpy()
-    want = orc.correlations(N, st, pairs, "ss", v.real) + orc.correlations(N, st, pairs, "ss", v.imag)
-    assert np.abs(got - want).max() < 1e-10
-    with pytest.raises(A.XDError):
-        basis.correlations(psi, pairs, "zz")
+    lift = orc.SymBlock(N, nup, perms, chi).lift(st)
+    for scale in (1.0, 2.5):
+        ps = psi * scale
+        v = lift @ ps.cpu().numpy()
+        for kind in ("ss", "zz"):
+            got = basis.correlations(ps, pairs, kind)
+            want = orc.correlations(N, st, pairs, kind, v.real) + orc.correlations(N, st, pairs, kind, v.imag)
+            assert np.abs(got - want).max() < 1e-10 * scale ** 2
 
 
 @pytest.mark.parametrize("case", [0, 2])
