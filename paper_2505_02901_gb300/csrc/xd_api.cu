@@ -466,6 +466,7 @@ static xd_status set_J(xd_ham_s *h, const double *J) {
     if (b->blk.ok) XD_TRY(block_ham_tables(h));
     if (b->spmm.ok) XD_TRY(spmm_ham_tables(h));
     if (b->spmm.ok) XD_TRY(passes_tables(h));
+    lanczos_forget(h, false);
     return XD_OK;
 }
 
@@ -506,6 +507,7 @@ xd_status xd_ham_set_couplings(xd_ham h, const double *J) {
 void xd_ham_destroy(xd_ham h) {
     if (!h) return;
     batch_forget(h);
+    lanczos_forget(h, true);
     cudaFree(h->d_J);
     cudaFree(h->d_bond);
     cudaFree(h->d_lzpart);

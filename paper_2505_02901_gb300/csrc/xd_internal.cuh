@@ -203,6 +203,16 @@ struct xd_ham_s {
     int x64_dcross_i = 0, x64_B = 0;
     void *d_x64_x = nullptr;        // workspace, 8 bytes per row (allocated on first use)
     int *d_x64_state = nullptr;     // [E, mode] and the statistics partials
+    // first Lanczos pass (xd_lanczos.cu): its stream, device state and, for
+    // small blocks, the captured steps with their three vectors (dropped when
+    // the couplings change: the captured kernels hold values derived from them)
+    cudaStream_t lz_stream = nullptr;
+    void *lz_dstate = nullptr, *lz_hstate = nullptr;
+    double *lz_ab = nullptr;
+    int lz_ab_cap = 0;
+    cudaGraphExec_t lz_exec = nullptr;
+    void *lz_buf[3] = {nullptr, nullptr, nullptr};
+    int lz_key_dt = -1, lz_key_iter = 0;
 };
 
 namespace xd {
@@ -256,6 +266,9 @@ bool spmm8_usable(const xd_ham_s *h, const void *x, const void *y);
 xd_status spmm8_apply(const xd_ham_s *h, const void *x, void *y, cudaStream_t st);
 // forget cached batch plans that use this handle (xd_batch.cu)
 void batch_forget(const xd_ham_s *h);
+// drop the first Lanczos pass's captured steps (and with all = true its stream
+// and buffers) (xd_lanczos.cu)
+void lanczos_forget(xd_ham_s *h, bool all);
 // workspace helper
 xd_status ensure_partials(xd_ham_s *h, size_t bytes);
 

@@ -171,6 +171,103 @@ __global__ void __launch_bounds__(kThreads) k_axpby_dot8(int64_t rows, double *_
     }
 }
 
+// ---------------------------------------- device-resident Lanczos steps
+// The first Lanczos pass keeps its scalars on the device.  A step is the
+// product w = H u, then k_lz_axpby1: w = sig w + cz up with <w, u>, whose
+// last CTA to finish sums the CTA partials in a fixed order and sets alpha,
+// then k_lz_axpby2: w = w + ca u with <w, w>, whose last CTA sets beta, the
+// stop test and the next step's coefficients.  When beta falls below 1e-13
+// max|alpha| (or is zero) or the step budget is spent, `done` is set and
+// every later vector kernel returns at once, so the host can replay captured
+// steps and look at the flag only every few steps.
+struct LzDev {
+    double sig;     // 1 / |w| of the current vector (its normalisation)
+    double cz;      // -beta_{k-1} sig_{k-1}: coefficient of the previous vector
+    double ca;      // -alpha_k sig_k
+    double amax;    // max |alpha| so far
+    int k;          // steps done
+    int done;       // 1 once the run has stopped
+    int max_iter;
+    unsigned arrived;  // CTAs done with the current vector kernel
+};
+
+// The last CTA of a grid to store its partial returns true (and has the
+// other CTAs' partials visible); the counter is reset for the next kernel.
+__device__ __forceinline__ bool last_cta(LzDev *sd) {
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&sd->arrived, 1u) == gridDim.x - 1;
+        if (last) sd->arrived = 0;
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// sum of n CTA partials by one warp: lane l adds entries l, l + 32, ... in
+// order, then a fixed shuffle tree (the same order on every call)
+__device__ __forceinline__ double warp_sum_parts(const double *part, int n) {
+    const int lane = threadIdx.x & 31;
+    double d = 0.0;
+    for (int i = lane; i < n; i += 32) d += __ldcg(part + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    return d;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_lz_axpby1(int64_t n, T *__restrict__ w, const T *__restrict__ up,
+                                                        const T *__restrict__ u, LzDev *sd, double *part,
+                                                        double *__restrict__ alpha) {
+    if (sd->done) return;
+    const T a = (T)sd->sig, c = (T)sd->cz;
+    typename AccOf<T>::A acc;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T t = a * w[i] + c * up[i];
+        w[i] = t;
+        acc.add(t, u[i]);
+    }
+    block_store(acc.get(), part);
+    if (last_cta(sd) && threadIdx.x < 32) {
+        // alpha_k = sig <w, u>
+        const double al = sd->sig * warp_sum_parts(part, gridDim.x);
+        if (threadIdx.x == 0) {
+            alpha[sd->k] = al;
+            sd->ca = -al * sd->sig;
+            sd->amax = fmax(sd->amax, fabs(al));
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_lz_axpby2(int64_t n, T *__restrict__ w, const T *__restrict__ u,
+                                                        LzDev *sd, double *part, double *__restrict__ beta) {
+    if (sd->done) return;
+    const T c = (T)sd->ca;
+    typename AccOf<T>::A acc;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T t = w[i] + c * u[i];
+        w[i] = t;
+        acc.add(t, t);
+    }
+    block_store(acc.get(), part);
+    if (last_cta(sd) && threadIdx.x < 32) {
+        // beta_k = |w|; the stop test; the next step's coefficients
+        const double bt = sqrt(fmax(warp_sum_parts(part, gridDim.x), 0.0));
+        if (threadIdx.x) return;
+        beta[sd->k] = bt;
+        sd->k += 1;
+        if (!(bt > 0.0) || bt < 1e-13 * sd->amax || sd->k >= sd->max_iter) {
+            sd->done = 1;
+        } else {
+            sd->cz = -bt * sd->sig;
+            sd->sig = 1.0 / bt;
+        }
+    }
+}
+
 // out[c] = sum over CTAs of part[cta][c], fixed order
 __global__ void k_sum8(const double *__restrict__ part, int n, double *__restrict__ out) {
     if (threadIdx.x >= 8 || blockIdx.x) return;
@@ -192,11 +289,11 @@ __global__ void k_axpy_c(int64_t n, double2 *__restrict__ out, double cr, double
     }
 }
 
+// *out = sum of n partials (one warp, the fixed order of warp_sum_parts)
 __global__ void k_sum(const double *__restrict__ part, int n, double *__restrict__ out) {
-    if (threadIdx.x || blockIdx.x) return;
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += part[i];
-    *out = s;
+    if (blockIdx.x || threadIdx.x >= 32) return;
+    const double s = warp_sum_parts(part, n);
+    if (threadIdx.x == 0) *out = s;
 }
 
 }  // namespace
@@ -214,6 +311,7 @@ xd_status vec_random(int64_t n, uint64_t seed, void *out, xd_dtype dt, cudaStrea
 
 static xd_status ensure_lanczos_partials(xd_ham_s *h, int n) {
     if (h->lzpart_n >= n) return XD_OK;
+    lanczos_forget(h, false);  // captured steps write into the old partials
     cudaFree(h->d_lzpart);
     h->d_lzpart = nullptr;
     h->lzpart_n = 0;
@@ -245,11 +343,185 @@ static xd_status lz_axpby(int64_t n, T *w, double a, const T *z, double c, const
     return XD_OK;
 }
 
-// One Lanczos run.  With coef != NULL it is the second pass: it reuses the
-// recorded alpha/beta and accumulates psi = sum_k coef[k] v_k.
+// The first Lanczos pass with its scalars on the device: three steps (one
+// turn of the three vectors' roles) are captured in a CUDA graph on a
+// stream of the handle's own and replayed; the host reads the state every
+// few replays (every replay once the products are costly, so that at most
+// two products run after the stop).  A product is run once before the capture so that its
+// tables and workspaces exist.  For blocks whose three vectors take at most
+// kLzKeep bytes the captured steps and their vectors stay with the handle
+// for the next run of the same storage and step budget (dropped when the
+// couplings change); larger runs free them at the end.
+constexpr int kLzCheckSmall = 8;       // replays between looks at the state, blocks below 2^20 rows
+constexpr size_t kLzKeep = 256u << 20;
+
+void lanczos_forget(xd_ham_s *h, bool all) {
+    if (h->lz_exec) cudaGraphExecDestroy(h->lz_exec);
+    h->lz_exec = nullptr;
+    for (int q = 0; q < 3; ++q) {
+        cudaFree(h->lz_buf[q]);
+        h->lz_buf[q] = nullptr;
+    }
+    h->lz_key_dt = -1;
+    h->lz_key_iter = 0;
+    if (!all) return;
+    if (h->lz_stream) cudaStreamDestroy(h->lz_stream);
+    h->lz_stream = nullptr;
+    cudaFree(h->lz_dstate);
+    h->lz_dstate = nullptr;
+    if (h->lz_hstate) cudaFreeHost(h->lz_hstate);
+    h->lz_hstate = nullptr;
+    cudaFree(h->lz_ab);
+    h->lz_ab = nullptr;
+    h->lz_ab_cap = 0;
+}
+
+template <typename T>
+static xd_status lanczos_pass1_graph(xd_ham_s *h, int max_iter, uint64_t seed, xd_dtype dt, double *alpha,
+                                     double *beta, int *n_iter) {
+    const xd_basis_s *b = h->b;
+    const int64_t n = b->dim * (b->cplx ? 2 : 1);
+    const size_t vbytes = (size_t)n * sizeof(T);
+    const bool keep = 3 * vbytes <= kLzKeep;
+    LzWork lw;
+    lw.grid = grid_for(n, kThreads, 8);
+    XD_TRY(ensure_lanczos_partials(h, 2 * lw.grid));
+    lw.part = h->d_lzpart;
+    lw.scal = h->d_scal;
+    double *part1 = h->d_lzpart, *part2 = h->d_lzpart + lw.grid;
+    cudaError_t e = cudaSuccess;
+    if (!h->lz_stream) e = cudaStreamCreateWithFlags(&h->lz_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !h->lz_dstate) e = dev_malloc(&h->lz_dstate, sizeof(LzDev));
+    if (e == cudaSuccess && !h->lz_hstate) e = cudaMallocHost(&h->lz_hstate, sizeof(LzDev));
+    if (e == cudaSuccess && h->lz_ab_cap < max_iter) {
+        cudaFree(h->lz_ab);
+        h->lz_ab = nullptr;
+        h->lz_ab_cap = 0;
+        e = dev_malloc((void **)&h->lz_ab, sizeof(double) * 2 * (size_t)max_iter);
+        if (e == cudaSuccess) h->lz_ab_cap = max_iter;
+        lanczos_forget(h, false);  // the captured steps write into the old array
+    }
+    if (e != cudaSuccess) return cuda_status(e, "Lanczos workspace");
+    cudaStream_t st = h->lz_stream;
+    LzDev *d_sd = (LzDev *)h->lz_dstate, *h_sd = (LzDev *)h->lz_hstate;
+    double *d_ab = h->lz_ab;
+    const int abcap = h->lz_ab_cap;
+    const bool cached = h->lz_exec && h->lz_key_dt == (int)dt && h->lz_key_iter == max_iter;
+    if (!cached) lanczos_forget(h, false);
+    T *buf[3] = {(T *)h->lz_buf[0], (T *)h->lz_buf[1], (T *)h->lz_buf[2]};
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+        if (!buf[k]) e = dev_malloc_vec(h, (void **)&buf[k], std::max<size_t>(vbytes, 16));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = cached ? h->lz_exec : nullptr;
+    xd_status rc = e == cudaSuccess ? XD_OK : cuda_status(e, "cudaMalloc(Lanczos vectors)");
+    do {
+        if (rc != XD_OK) break;
+        T *up = buf[0], *u = buf[1], *w = buf[2];
+        if ((rc = vec_random(b->dim, seed, u, dt, st)) != XD_OK) break;
+        if ((e = cudaMemsetAsync(up, 0, vbytes, st)) != cudaSuccess) {
+            rc = cuda_status(e, "cudaMemsetAsync");
+            break;
+        }
+        double nrm2 = 0.0;
+        if ((rc = lz_axpby<T>(n, u, 1.0, nullptr, 0.0, u, lw, st, &nrm2)) != XD_OK) break;
+        if (!(nrm2 > 0.0)) {
+            set_error("Lanczos: zero start vector");
+            rc = XD_EINVAL;
+            break;
+        }
+        *h_sd = LzDev{1.0 / sqrt(nrm2), 0.0, 0.0, 0.0, 0, 0, max_iter, 0u};
+        if ((e = cudaMemcpyAsync(d_sd, h_sd, sizeof(LzDev), cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+            rc = cuda_status(e, "Lanczos state");
+            break;
+        }
+        if (!exec) {
+            // one product outside the capture (tables, workspaces)
+            if ((rc = xd_apply(h, u, w, dt, 1, (xd_stream)st)) != XD_OK) break;
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) {
+                rc = cuda_status(e, "Lanczos start");
+                break;
+            }
+            if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed)) != cudaSuccess) {
+                rc = cuda_status(e, "cudaStreamBeginCapture");
+                break;
+            }
+            xd_status cap = XD_OK;
+            T *cu = u, *cup = up, *cw = w;
+            for (int j = 0; j < 3 && cap == XD_OK; ++j) {
+                cap = xd_apply(h, cu, cw, dt, 1, (xd_stream)st);
+                if (cap != XD_OK) break;
+                k_lz_axpby1<T><<<lw.grid, kThreads, 0, st>>>(n, cw, cup, cu, d_sd, part1, d_ab);
+                k_lz_axpby2<T><<<lw.grid, kThreads, 0, st>>>(n, cw, cu, d_sd, part2, d_ab + abcap);
+                T *t = cup;
+                cup = cu;
+                cu = cw;
+                cw = t;
+            }
+            e = cudaStreamEndCapture(st, &graph);
+            if (cap != XD_OK) {
+                rc = cap;
+                break;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+            if (e != cudaSuccess) {
+                rc = cuda_status(e, "Lanczos graph");
+                break;
+            }
+        }
+        const int every = b->dim < (1 << 20) ? kLzCheckSmall : 1;
+        for (int rep = 0; e == cudaSuccess;) {
+            e = cudaGraphLaunch(exec, st);
+            if (e != cudaSuccess) break;
+            if (++rep % every == 0 || 3 * rep >= max_iter) {
+                e = cudaMemcpyAsync(h_sd, d_sd, sizeof(LzDev), cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                if (e == cudaSuccess && h_sd->done) break;
+            }
+        }
+        if (e != cudaSuccess) {
+            rc = cuda_status(e, "Lanczos steps");
+            break;
+        }
+        const int k = h_sd->k;
+        std::vector<double> ab(2 * (size_t)abcap);
+        e = cudaMemcpy(ab.data(), d_ab, sizeof(double) * ab.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            rc = cuda_status(e, "Lanczos coefficients");
+            break;
+        }
+        for (int q = 0; q < k; ++q) {
+            alpha[q] = ab[q];
+            beta[q] = ab[abcap + q];
+        }
+        *n_iter = k;
+    } while (0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamSynchronize(st);
+    if (rc == XD_OK && keep) {
+        h->lz_exec = exec;
+        for (int q = 0; q < 3; ++q) h->lz_buf[q] = buf[q];
+        h->lz_key_dt = (int)dt;
+        h->lz_key_iter = max_iter;
+    } else {
+        if (exec) cudaGraphExecDestroy(exec);
+        h->lz_exec = nullptr;
+        for (int q = 0; q < 3; ++q) {
+            cudaFree(buf[q]);
+            h->lz_buf[q] = nullptr;
+        }
+        h->lz_key_dt = -1;
+    }
+    return rc;
+}
+
+// One Lanczos run.  Without coef it is the first pass (device-resident,
+// lanczos_pass1_graph); with coef it is the second pass of eig0 (Sec.
+// 3.6.1): the same recurrence from the same start, with the recorded alpha
+// and beta, accumulating psi = sum_k coef[k] v_k.
 template <typename T>
 static xd_status lanczos_run(xd_ham_s *h, int max_iter, uint64_t seed, xd_dtype dt, double *alpha,
                              double *beta, int *n_iter, const double *coef, T *psi) {
+    if (!coef) return lanczos_pass1_graph<T>(h, max_iter, seed, dt, alpha, beta, n_iter);
     const xd_basis_s *b = h->b;
     const int64_t n = b->dim * (b->cplx ? 2 : 1);
     cudaStream_t st = 0;
@@ -283,38 +555,20 @@ static xd_status lanczos_run(xd_ham_s *h, int max_iter, uint64_t seed, xd_dtype 
             rc = XD_EINVAL;
             break;
         }
-        double sig = 1.0 / sqrt(nrm2), sig_prev = 0.0, beta_prev = 0.0, amax = 0.0;
-        int k = 0;
-        const int steps = coef ? *n_iter : max_iter;
-        for (k = 0; k < steps; ++k) {
-            if (coef) {
-                k_axpy<T><<<lw.grid, kThreads, 0, st>>>(n, psi, (T)(coef[k] * sig), u);
-                cudaError_t e = cudaGetLastError();
-                if (e != cudaSuccess) {
-                    rc = cuda_status(e, "k_axpy");
-                    break;
-                }
-                if (k == steps - 1) break;
-                if ((rc = xd_apply(h, u, w, dt, 1, (xd_stream)st)) != XD_OK) break;
-                if ((rc = lz_axpby<T>(n, w, sig, up, -beta_prev * sig_prev, nullptr, lw, st, nullptr)) != XD_OK) break;
-                if ((rc = lz_axpby<T>(n, w, 1.0, u, -alpha[k] * sig, nullptr, lw, st, nullptr)) != XD_OK) break;
-                beta_prev = beta[k];
-            } else {
-                if ((rc = xd_apply(h, u, w, dt, 1, (xd_stream)st)) != XD_OK) break;
-                double d1 = 0.0, d2 = 0.0;
-                if ((rc = lz_axpby<T>(n, w, sig, up, -beta_prev * sig_prev, u, lw, st, &d1)) != XD_OK) break;
-                const double a = sig * d1;
-                if ((rc = lz_axpby<T>(n, w, 1.0, u, -a * sig, w, lw, st, &d2)) != XD_OK) break;
-                const double bt = sqrt(std::max(d2, 0.0));
-                alpha[k] = a;
-                beta[k] = bt;
-                amax = std::max(amax, fabs(a));
-                beta_prev = bt;
-                if (bt < 1e-13 * amax || k == steps - 1) {
-                    ++k;
-                    break;
-                }
+        double sig = 1.0 / sqrt(nrm2), sig_prev = 0.0, beta_prev = 0.0;
+        const int steps = *n_iter;
+        for (int k = 0; k < steps; ++k) {
+            k_axpy<T><<<lw.grid, kThreads, 0, st>>>(n, psi, (T)(coef[k] * sig), u);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) {
+                rc = cuda_status(e, "k_axpy");
+                break;
             }
+            if (k == steps - 1) break;
+            if ((rc = xd_apply(h, u, w, dt, 1, (xd_stream)st)) != XD_OK) break;
+            if ((rc = lz_axpby<T>(n, w, sig, up, -beta_prev * sig_prev, nullptr, lw, st, nullptr)) != XD_OK) break;
+            if ((rc = lz_axpby<T>(n, w, 1.0, u, -alpha[k] * sig, nullptr, lw, st, nullptr)) != XD_OK) break;
+            beta_prev = beta[k];
             sig_prev = sig;
             sig = 1.0 / beta_prev;
             T *t = up;
@@ -322,8 +576,6 @@ static xd_status lanczos_run(xd_ham_s *h, int max_iter, uint64_t seed, xd_dtype 
             u = w;
             w = t;
         }
-        if (rc != XD_OK) break;
-        if (!coef) *n_iter = k;
     } while (0);
     cudaError_t e = cudaStreamSynchronize(st);
     for (int q = 0; q < 3; ++q) cudaFree(buf[q]);

@@ -1018,6 +1018,7 @@ static xd_status x64_workspace(xd_ham_s *h, int64_t dim) {
 
 void x64_release(xd_ham_s *h) {
     if (h->d_x64_x) {
+        lanczos_forget(h, false);  // captured Lanczos steps read the workspace
         cudaFree(h->d_x64_x);
         h->d_x64_x = nullptr;
     }
