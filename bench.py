@@ -550,14 +550,21 @@ def run_sym_chain(n: int):
 def run_space_group(lattice: str, nup: int):
     """The symmetric product on the 36-site torus with its full space group
     (square: translations x C4v, 288 elements, J1-J2; triangular:
-    translations x C6v, 432 elements), fully symmetric irrep, four times."""
+    translations x C6v, 432 elements) or its 36 translations alone (J1-J2,
+    momentum (0, 0)), fully symmetric irrep, four times."""
     import torch
 
     from paper_2505_02901_gb300 import api, build, workloads as W
     build.build()
-    bonds, J = W.square_j1j2(6, 6) if lattice == "square" else W.triangular(6)
-    perms = W.space_group(6, 6, lattice)
-    basis = api.Basis(36, nup, bonds, symmetry=(perms, W.space_group_characters(6, 6, lattice)))
+    if lattice == "translations":
+        bonds, J = W.square_j1j2(6, 6)
+        perms = W.torus_translations(6, 6)
+        chi = W.torus_characters(6, 6, 0, 0)
+    else:
+        bonds, J = W.square_j1j2(6, 6) if lattice == "square" else W.triangular(6)
+        perms = W.space_group(6, 6, lattice)
+        chi = W.space_group_characters(6, 6, lattice)
+    basis = api.Basis(36, nup, bonds, symmetry=(perms, chi))
     h = api.Hamiltonian(basis, J)
     x = api.random_vector(basis.dim, SEED, torch.float64)
     y = torch.empty_like(x)
@@ -609,11 +616,12 @@ def main():
                          "the symmetric product of the N-site chain with its translations and "
                          "reflections (fully symmetric irrep, N from --chain-n); space-group, the "
                          "symmetric product of the 36-site torus with its full space group "
-                         "(--group square or triangular, --nup); apply8, the "
+                         "(--group square or triangular) or its translations (--group translations), "
+                         "--nup; apply8, the "
                          "eight-vector FP32 product on the --lattice block; bilinear, the per-bond "
                          "forms of the 56-bond ladder (FP64)")
     ap.add_argument("--chain-n", type=int, default=32)
-    ap.add_argument("--group", default="square", choices=["square", "triangular"])
+    ap.add_argument("--group", default="square", choices=["square", "triangular", "translations"])
     ap.add_argument("--nup", type=int, default=18)
     ap.add_argument("--lattice", default="4x8",
                     help="LxxLy of the periodic J1-J2 lattice (4x8 is the benchmark; smaller "

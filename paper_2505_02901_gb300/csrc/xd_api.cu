@@ -223,6 +223,7 @@ static void free_basis(xd_basis_s *b) {
     cudaFree(b->d_act);
     cudaFree(b->d_minrot);
     cudaFree(b->d_amask);
+    cudaFree(b->d_rowtab);
     cudaFree(b->d_tg);
     cudaFree(b->d_tpp);
     cudaFree(b->d_pm);
@@ -263,6 +264,8 @@ xd::SymView xd_basis_s::symview() const {
     v.ty = ty;
     v.minrot = d_minrot;
     v.amask = d_amask;
+    v.rowtab = d_rowtab;
+    v.trep1 = trep1;
     v.tg = d_tg;
     v.tnp = tnp;
     v.tpp = d_tpp;
@@ -467,6 +470,7 @@ static xd_status set_J(xd_ham_s *h, const double *J) {
     if (b->spmm.ok) XD_TRY(spmm_ham_tables(h));
     if (b->spmm.ok) XD_TRY(passes_tables(h));
     lanczos_forget(h, false);
+    batch_forget(h);  // captured batched launches hold per-coupling scalars
     return XD_OK;
 }
 

@@ -10,12 +10,18 @@
 // row, read and written as one contiguous [nvec] record.
 //
 // Schedule: the threads per CTA and the rows per tile are chosen by a small
-// autotuner that times every candidate once (CUDA events) the first time a
-// batch is seen; the chosen launch is captured in a CUDA graph and replayed
-// while the batch (handles, vectors, dtype, nvec, stream) is unchanged.
-// Instances large enough for the prefix-block layout (N >= 24) with eight
-// FP32 right-hand sides leave the persistent launch: each gets the
-// eight-vector prefix-block product (xd_u1_spmm8.cu), in the same graph.
+// autotuner that takes the median of five timings of every candidate (CUDA
+// events) the first time a batch is seen; the chosen launch is captured in a
+// CUDA graph and replayed while the batch (handles, vectors, dtype, nvec,
+// stream) is unchanged.
+//
+// Eight FP32 right-hand sides with operators large enough for the prefix
+// block layout (N >= 24): one persistent launch of k_batch8 does the whole
+// batch.  Its work list is every prefix block of the large operators (the
+// eight-vector product of xd_u1_spmm8.cu, one block per unit, largest
+// operators first) followed by the row tiles of the small ones; a CTA takes
+// the next unit from a counter in device memory, which the last CTA to
+// finish resets for the next launch.
 
 #include <algorithm>
 #include <map>
@@ -23,6 +29,7 @@
 #include <vector>
 
 #include "xd_internal.cuh"
+#include "xd_spmm8.cuh"
 
 namespace xd {
 
@@ -48,6 +55,68 @@ __device__ __forceinline__ uint64_t find_block(const int64_t *__restrict__ hi_of
     return lo;
 }
 
+// Rows [row0, row1) of instance I (bond table staged in sm_mask / sm_half).
+template <typename T, int NV>
+__device__ __forceinline__ void batch_rows(const Inst &I, const uint64_t *sm_mask, const T *sm_half,
+                                           uint64_t *sh_range, int64_t row0, int64_t row1) {
+    const U1View &u = I.u;
+    if (threadIdx.x == 0) {
+        uint64_t nh = 1ull << u.P;
+        uint64_t h0 = find_block(u.hi_off, 0, nh - 1, row0);
+        sh_range[0] = h0;
+        sh_range[1] = find_block(u.hi_off, h0, nh - 1, row1 - 1);
+    }
+    __syncthreads();
+    const T jq = (T)I.bond[2 * I.nb];
+    const T *__restrict__ x = (const T *)I.x;
+    T *__restrict__ y = (T *)I.y;
+    for (int64_t r = row0 + threadIdx.x; r < row1; r += blockDim.x) {
+        const uint64_t h = find_block(u.hi_off, sh_range[0], sh_range[1], r);
+        const int m = u.nup - __popcll(h);
+        const uint32_t l = __ldg(u.lo_list + __ldg(u.lo_off + m) + (uint32_t)(r - __ldg(u.hi_off + h)));
+        const uint64_t s = (h << u.L) | l;
+        T acc[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] = T(0);
+        T dsub = T(0);
+        for (int b = 0; b < I.nb; ++b) {
+            const uint64_t mk = sm_mask[b];
+            const uint64_t tt = s & mk;
+            if (tt != 0 && tt != mk) {
+                const uint64_t f = s ^ mk;
+                const int64_t c = __ldg(u.hi_off + (f >> u.L)) + (int64_t)__ldg(u.lo_rank + (f & u.lomask));
+                const T cf = sm_half[b];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) acc[q] += cf * __ldg(x + c * NV + q);
+                dsub += cf;
+            }
+        }
+        const T d = jq - dsub;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) y[r * NV + q] = d * __ldg(x + r * NV + q) + acc[q];
+    }
+}
+
+// Stages the bond table of instance I.
+template <typename T>
+__device__ __forceinline__ void batch_stage(const Inst &I, uint64_t *sm_mask, T *sm_half) {
+    const uint64_t *masks = (const uint64_t *)(I.bond + I.nb);
+    for (int b = threadIdx.x; b < I.nb; b += blockDim.x) {
+        sm_mask[b] = masks[b];
+        sm_half[b] = (T)(0.5 * I.bond[b]);
+    }
+}
+
+// Instance of global tile t: the last with tile0 <= t.
+__device__ __forceinline__ int batch_find(const Inst *__restrict__ inst, int ninst, int64_t t) {
+    int lo = 0, hi = ninst - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (inst[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 template <typename T, int NV>
 __global__ void k_batch(const Inst *__restrict__ inst, int ninst, int64_t ntiles, int tile_rows) {
     __shared__ uint64_t sm_mask[kMaxBatchBonds];
@@ -56,64 +125,107 @@ __global__ void k_batch(const Inst *__restrict__ inst, int ninst, int64_t ntiles
     __shared__ uint64_t sh_range[2];
     int cur = -1;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        if (threadIdx.x == 0) {
-            int lo = 0, hi = ninst - 1;  // last instance with tile0 <= t
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (inst[mid].tile0 <= t) lo = mid; else hi = mid - 1;
-            }
-            sh_k = lo;
-        }
+        if (threadIdx.x == 0) sh_k = batch_find(inst, ninst, t);
         __syncthreads();
         const int k = sh_k;
         const Inst &I = inst[k];
-        const U1View &u = I.u;
         if (k != cur) {
-            const uint64_t *masks = (const uint64_t *)(I.bond + I.nb);
-            for (int b = threadIdx.x; b < I.nb; b += blockDim.x) {
-                sm_mask[b] = masks[b];
-                sm_half[b] = (T)(0.5 * I.bond[b]);
-            }
+            batch_stage(I, sm_mask, sm_half);
             cur = k;
         }
         const int64_t row0 = (t - I.tile0) * tile_rows;
-        const int64_t row1 = min(row0 + (int64_t)tile_rows, u.dim);
-        if (threadIdx.x == 0) {
-            uint64_t nh = 1ull << u.P;
-            uint64_t h0 = find_block(u.hi_off, 0, nh - 1, row0);
-            sh_range[0] = h0;
-            sh_range[1] = find_block(u.hi_off, h0, nh - 1, row1 - 1);
-        }
+        batch_rows<T, NV>(I, sm_mask, sm_half, sh_range, row0, min(row0 + (int64_t)tile_rows, I.u.dim));
         __syncthreads();
-        const T jq = (T)I.bond[2 * I.nb];
-        const T *__restrict__ x = (const T *)I.x;
-        T *__restrict__ y = (T *)I.y;
-        for (int64_t r = row0 + threadIdx.x; r < row1; r += blockDim.x) {
-            const uint64_t h = find_block(u.hi_off, sh_range[0], sh_range[1], r);
-            const int m = u.nup - __popcll(h);
-            const uint32_t l = __ldg(u.lo_list + __ldg(u.lo_off + m) + (uint32_t)(r - __ldg(u.hi_off + h)));
-            const uint64_t s = (h << u.L) | l;
-            T acc[NV];
-#pragma unroll
-            for (int q = 0; q < NV; ++q) acc[q] = T(0);
-            T dsub = T(0);
-            for (int b = 0; b < I.nb; ++b) {
-                const uint64_t mk = sm_mask[b];
-                const uint64_t tt = s & mk;
-                if (tt != 0 && tt != mk) {
-                    const uint64_t f = s ^ mk;
-                    const int64_t c = __ldg(u.hi_off + (f >> u.L)) + (int64_t)__ldg(u.lo_rank + (f & u.lomask));
-                    const T cf = sm_half[b];
-#pragma unroll
-                    for (int q = 0; q < NV; ++q) acc[q] += cf * __ldg(x + c * NV + q);
-                    dsub += cf;
+    }
+}
+
+// One large operator of the fused launch.
+struct Big8 {
+    sp8::Sp8Params p;
+    const float *x;
+    float *y;
+    int L;
+    int64_t unit0;  // its first work unit
+};
+
+// Arguments of the fused launch; the large operators' parameters sit in the
+// kernel's parameter space, so that their fields are constant-bank operands.
+constexpr int kMaxBig8 = 96;
+
+struct Batch8Args {
+    int nbig, ninst, tile_rows;
+    int64_t ubig, ntiles;
+    const Inst *inst;
+    unsigned long long *ctr;
+    Big8 big[kMaxBig8];
+};
+
+// FP32, eight right-hand sides: the prefix blocks of the large operators
+// (units [0, ubig)) and the row tiles of the small ones (units [ubig,
+// ubig + ntiles)), one unit at a time from ctr[0]; ctr[1] counts the CTAs
+// that are done.
+__global__ void __launch_bounds__(sp8::kT8, 2) k_batch8(const __grid_constant__ Batch8Args a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int sh_k;
+    __shared__ long long sh_t;
+    __shared__ uint64_t sm_mask[kMaxBatchBonds];
+    __shared__ float sm_half[kMaxBatchBonds];
+    __shared__ uint64_t sh_range[2];
+    int cur_big = -1, cur_small = -1;
+    const int64_t total = a.ubig + a.ntiles;
+    for (;;) {
+        if (threadIdx.x == 0) sh_t = (long long)atomicAdd(a.ctr, 1ull);
+        __syncthreads();
+        const int64_t t = sh_t;
+        if (t >= total) break;
+        if (t < a.ubig) {
+            int q = 0;  // last operator with unit0 <= t (the same in every thread)
+            {
+                int hi = a.nbig - 1;
+                while (q < hi) {
+                    int mid = (q + hi + 1) >> 1;
+                    if (a.big[mid].unit0 <= t) q = mid; else hi = mid - 1;
                 }
             }
-            const T d = jq - dsub;
-#pragma unroll
-            for (int q = 0; q < NV; ++q) y[r * NV + q] = d * __ldg(x + r * NV + q) + acc[q];
+            const Big8 &B = a.big[q];
+            if (q != cur_big) {  // block() starts with a barrier, after which the tables are seen
+                switch (B.L) {
+                    case 12: sp8::tables<12>(B.p, smem); break;
+                    case 11: sp8::tables<11>(B.p, smem); break;
+                    default: sp8::tables<10>(B.p, smem);
+                }
+                cur_big = q;
+            }
+            const uint32_t h = __ldg(B.p.items + (t - B.unit0));
+            if (h != sp8::kEmpty8) {
+                switch (B.L) {
+                    case 12: sp8::block<12>(B.p, smem, h, B.x, B.y); break;
+                    case 11: sp8::block<11>(B.p, smem, h, B.x, B.y); break;
+                    default: sp8::block<10>(B.p, smem, h, B.x, B.y);
+                }
+            }
+        } else {
+            const int64_t tt = t - a.ubig;
+            if (threadIdx.x == 0) sh_k = batch_find(a.inst, a.ninst, tt);
+            __syncthreads();
+            const int k = sh_k;
+            const Inst &I = a.inst[k];
+            if (k != cur_small) {
+                batch_stage(I, sm_mask, sm_half);
+                cur_small = k;
+            }
+            const int64_t row0 = (tt - I.tile0) * a.tile_rows;
+            batch_rows<float, 8>(I, sm_mask, sm_half, sh_range, row0, min(row0 + (int64_t)a.tile_rows, I.u.dim));
         }
-        __syncthreads();
+        __syncthreads();  // unit done: shared state may be overwritten
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.ctr + 1, 1ull) == (unsigned long long)gridDim.x - 1) {
+            a.ctr[0] = 0;  // every CTA has taken its last unit
+            a.ctr[1] = 0;
+            __threadfence();
+        }
     }
 }
 
@@ -121,16 +233,29 @@ struct Plan {
     std::vector<const xd_ham_s *> hs;
     std::vector<const void *> xs;
     std::vector<void *> ys;
-    std::vector<int> rest, big;  // instances of the persistent launch / of their own launch
+    std::vector<int> rest, big;  // small instances (row tiles) / large ones (prefix blocks, k_batch8)
     xd_dtype dt;
     int nvec;
     cudaStream_t st;
     Inst *d_inst = nullptr;
     int64_t ntiles = 0;
     int threads = 256, tile_rows = 1024, grid = 1;
+    // fused launch (big non-empty)
+    std::vector<Big8> hbig;
+    int64_t ubig = 0;
+    unsigned long long *d_ctr = nullptr;
+    size_t smem8 = 0;
+    int per_sm8 = 1;
     cudaGraphExec_t exec = nullptr;
     bool tuned = false;
 };
+
+void free_plan(Plan *p) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    cudaFree(p->d_inst);
+    cudaFree(p->d_ctr);
+    delete p;
+}
 
 std::mutex g_mu;
 std::vector<Plan *> g_plans;
@@ -140,9 +265,19 @@ void launch(const Plan &p, cudaStream_t st) {
     k_batch<T, NV><<<p.grid, p.threads, 0, st>>>(p.d_inst, (int)p.rest.size(), p.ntiles, p.tile_rows);
 }
 
-void launch_rest(const Plan &p, cudaStream_t st) {
-    if (p.rest.empty()) return;
-    if (p.dt == XD_F64) {
+xd_status launch_any(const Plan &p, cudaStream_t st) {
+    if (!p.big.empty()) {
+        Batch8Args a;
+        a.nbig = (int)p.hbig.size();
+        a.ninst = (int)p.rest.size();
+        a.tile_rows = p.tile_rows;
+        a.ubig = p.ubig;
+        a.ntiles = p.ntiles;
+        a.inst = p.d_inst;
+        a.ctr = p.d_ctr;
+        std::copy(p.hbig.begin(), p.hbig.end(), a.big);
+        k_batch8<<<p.grid, sp8::kT8, p.smem8, st>>>(a);
+    } else if (p.dt == XD_F64) {
         switch (p.nvec) {
             case 1: launch<double, 1>(p, st); break;
             case 2: launch<double, 2>(p, st); break;
@@ -157,15 +292,11 @@ void launch_rest(const Plan &p, cudaStream_t st) {
             default: launch<float, 8>(p, st);
         }
     }
-}
-
-xd_status launch_any(const Plan &p, cudaStream_t st) {
-    launch_rest(p, st);
     XD_CUDA(cudaGetLastError());
-    for (int k : p.big) XD_TRY(spmm8_apply(p.hs[k], p.xs[k], p.ys[k], st));
     return XD_OK;
 }
 
+// Row tiles of the small instances for the current tile_rows; the grid.
 xd_status build_table(Plan *p) {
     std::vector<Inst> h(p->rest.size());
     int64_t tiles = 0;
@@ -181,48 +312,96 @@ xd_status build_table(Plan *p) {
         tiles += (hm->b->dim + p->tile_rows - 1) / p->tile_rows;
     }
     p->ntiles = tiles;
+    const int64_t units = p->ubig + tiles;
+    const int64_t resident = p->big.empty() ? (int64_t)g_num_sms * (2048 / p->threads) : (int64_t)g_num_sms * p->per_sm8;
+    p->grid = (int)std::max<int64_t>(1, std::min<int64_t>(units, resident));
     if (h.empty()) return XD_OK;
     if (!p->d_inst) XD_CUDA(dev_malloc((void **)&p->d_inst, sizeof(Inst) * h.size()));
     XD_CUDA(cudaMemcpy(p->d_inst, h.data(), sizeof(Inst) * h.size(), cudaMemcpyHostToDevice));
     return XD_OK;
 }
 
-// Time each (threads, rows per tile) candidate once and keep the fastest.
+// Work units of the large operators (largest first), the unit counter and
+// the fused kernel's shared memory.
+xd_status build_big(Plan *p) {
+    std::stable_sort(p->big.begin(), p->big.end(),
+                     [&](int a, int b) { return p->hs[a]->b->dim > p->hs[b]->b->dim; });
+    std::vector<Big8> h(p->big.size());
+    int64_t units = 0;
+    size_t smem = 0;
+    for (size_t q = 0; q < p->big.size(); ++q) {
+        const int k = p->big[q];
+        sp8_params(p->hs[k], &h[q].p);
+        h[q].x = (const float *)p->xs[k];
+        h[q].y = (float *)p->ys[k];
+        h[q].L = p->hs[k]->b->spmm.L;
+        if (h[q].L < 10 || h[q].L > 12) {
+            set_error("batched product: postfix length %d not supported", h[q].L);
+            return XD_ERANGE;
+        }
+        h[q].unit0 = units;
+        units += h[q].p.nprefix;
+        const int mb = h[q].L == 12 ? sp8::Sp8Geo<12>::maxblk : h[q].L == 11 ? sp8::Sp8Geo<11>::maxblk
+                                                                              : sp8::Sp8Geo<10>::maxblk;
+        smem = std::max(smem, sp8::Sp8Smem(h[q].p, mb).total);
+    }
+    p->ubig = units;
+    p->smem8 = smem;
+    XD_CUDA(cudaFuncSetAttribute(k_batch8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    XD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->per_sm8, k_batch8, sp8::kT8, smem));
+    if (p->per_sm8 < 1) {
+        set_error("batched product: %zu bytes of shared memory do not fit", smem);
+        return XD_ERANGE;
+    }
+    p->hbig = h;
+    XD_CUDA(dev_malloc((void **)&p->d_ctr, 2 * sizeof(unsigned long long)));
+    XD_CUDA(cudaMemset(p->d_ctr, 0, 2 * sizeof(unsigned long long)));
+    return XD_OK;
+}
+
+// Time each (threads, rows per tile) candidate kTuneReps times after one
+// warm launch and keep the one with the smallest median.  The fused launch
+// has 512 threads; only its rows per tile are tuned.
+constexpr int kTuneReps = 5;
+
 xd_status autotune(Plan *p) {
-    for (int k : p->big) XD_TRY(spmm8_apply(p->hs[k], p->xs[k], p->ys[k], p->st));  // attributes, warm
+    if (!p->big.empty()) XD_TRY(build_big(p));
     if (p->rest.empty()) {
+        XD_TRY(build_table(p));
         p->tuned = true;
         return XD_OK;
     }
-    const int cand_threads[] = {128, 256, 512};
+    std::vector<int> cand_threads = {128, 256, 512};
+    if (!p->big.empty()) cand_threads = {sp8::kT8};
     const int cand_rows_per_thread[] = {1, 4, 16};
     struct Events {  // destroyed on every return path
-        cudaEvent_t a = nullptr, b = nullptr;
+        cudaEvent_t e[kTuneReps + 1] = {};
         ~Events() {
-            if (a) cudaEventDestroy(a);
-            if (b) cudaEventDestroy(b);
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
         }
     } ev;
-    XD_CUDA(cudaEventCreate(&ev.a));
-    XD_CUDA(cudaEventCreate(&ev.b));
-    cudaEvent_t e0 = ev.a, e1 = ev.b;
+    for (cudaEvent_t &x : ev.e) XD_CUDA(cudaEventCreate(&x));
     float best = 1e30f;
-    int bt = 256, br = 1024;
+    int bt = cand_threads[0], br = cand_threads[0];
     for (int th : cand_threads)
         for (int rpt : cand_rows_per_thread) {
             p->threads = th;
             p->tile_rows = th * rpt;
             XD_TRY(build_table(p));
-            p->grid = (int)std::max<int64_t>(1, std::min<int64_t>(p->ntiles, (int64_t)g_num_sms * (2048 / th)));
-            launch_rest(*p, p->st);  // warm
-            XD_CUDA(cudaEventRecord(e0, p->st));
-            launch_rest(*p, p->st);
-            XD_CUDA(cudaEventRecord(e1, p->st));
-            XD_CUDA(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            XD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) {
-                best = ms;
+            XD_TRY(launch_any(*p, p->st));  // warm
+            XD_CUDA(cudaEventRecord(ev.e[0], p->st));
+            for (int r = 0; r < kTuneReps; ++r) {
+                XD_TRY(launch_any(*p, p->st));
+                XD_CUDA(cudaEventRecord(ev.e[r + 1], p->st));
+            }
+            XD_CUDA(cudaEventSynchronize(ev.e[kTuneReps]));
+            float ms[kTuneReps];
+            for (int r = 0; r < kTuneReps; ++r) XD_CUDA(cudaEventElapsedTime(&ms[r], ev.e[r], ev.e[r + 1]));
+            std::sort(ms, ms + kTuneReps);
+            const float med = ms[kTuneReps / 2];
+            if (med < best) {
+                best = med;
                 bt = th;
                 br = th * rpt;
             }
@@ -230,7 +409,6 @@ xd_status autotune(Plan *p) {
     p->threads = bt;
     p->tile_rows = br;
     XD_TRY(build_table(p));
-    p->grid = (int)std::max<int64_t>(1, std::min<int64_t>(p->ntiles, (int64_t)g_num_sms * (2048 / bt)));
     p->tuned = true;
     return XD_OK;
 }
@@ -259,9 +437,7 @@ void batch_forget(const xd_ham_s *h) {
     for (auto it = g_plans.begin(); it != g_plans.end();) {
         Plan *p = *it;
         if (std::find(p->hs.begin(), p->hs.end(), h) != p->hs.end()) {
-            if (p->exec) cudaGraphExecDestroy(p->exec);
-            cudaFree(p->d_inst);
-            delete p;
+            free_plan(p);
             it = g_plans.erase(it);
         } else {
             ++it;
@@ -324,15 +500,15 @@ extern "C" xd_status xd_batch_apply(int ninst, const xd_ham *hs, const void *con
         plan->nvec = nvec;
         plan->st = st;
         for (int k = 0; k < ninst; ++k) {
-            if (dt == XD_F32 && nvec == 8 && spmm8_usable(hs[k], xs[k], ys[k])) plan->big.push_back(k);
-            else plan->rest.push_back(k);
+            if (dt == XD_F32 && nvec == 8 && (int)plan->big.size() < kMaxBig8 && spmm8_usable(hs[k], xs[k], ys[k]))
+                plan->big.push_back(k);
+            else
+                plan->rest.push_back(k);
         }
         xd_status s = autotune(plan);
         if (s == XD_OK) s = capture(plan);
         if (s != XD_OK) {
-            if (plan->exec) cudaGraphExecDestroy(plan->exec);
-            cudaFree(plan->d_inst);
-            delete plan;
+            free_plan(plan);
             return s;
         }
         g_plans.push_back(plan);

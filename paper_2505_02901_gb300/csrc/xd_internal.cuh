@@ -75,6 +75,9 @@ struct SymView {
     // element s -> T_{a,b}(p_k s).  tnp = 0: translations only.
     int tx, ty, tnp;
     const uint8_t *minrot, *amask;
+    // rowtab[r] = minrot[r] | amask[r] << 8; trep1 = bit 0 of every row
+    const uint16_t *rowtab;
+    uint64_t trep1;
     const int16_t *tg, *tpp;
     // pm[(k - 1) nb + b] = p_k applied to the mask of bond b (k >= 1): the
     // action is linear over XOR, so p_k(s ^ m) = p_k(s) ^ p_k(m)
@@ -163,6 +166,8 @@ struct xd_basis_s {
     int nchunk = 0;
     int tx = 0, ty = 0, tnp = 0;     // detected torus translations (and their cosets)
     uint8_t *d_minrot = nullptr, *d_amask = nullptr;
+    uint16_t *d_rowtab = nullptr;
+    uint64_t trep1 = 0;
     int16_t *d_tg = nullptr, *d_tpp = nullptr;
     uint64_t *d_pm = nullptr;        // point images of the bond masks
     int cn = 0, cdih = 0;            // detected ring rotations (+ reflections)

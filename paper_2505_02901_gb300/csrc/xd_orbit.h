@@ -1,0 +1,184 @@
+// xd_orbit.h -- the representative of a word under a group holding the
+// translations of an Lx x Ly torus (Sec. 3.10: the representative of an
+// orbit is its smallest image), for host and device code.
+//
+// The group is the union of the cosets {s -> T_{a,b}(p_k s)} (p_0 the
+// identity; T alone when there is one coset).  (T_{a,b} w) puts in row y the
+// row (y + b) mod Ly of w rotated by a (new bit x = old bit (x + a) mod Lx);
+// row Ly - 1 holds the most significant bits.  The smallest image of w over
+// T therefore has as top row the smallest rotation of any row of w, and is
+// found row by row from the top: a candidate set of translations (a, b) is
+// cut, row by row, to those reaching the smallest value of that row.  Once
+// one candidate is left its image is formed in one go.  Across cosets the
+// running smallest image bounds the search: a coset whose partial image
+// exceeds it stops.
+//
+// Candidates are the bits a + 8 b of a 64-bit word (Lx <= 8, Ly <= 8).
+// Tables: rowtab[r] = smallest rotation of the Lx-bit row r (low byte) and
+// the mask of the rotations a reaching it (high byte).
+
+#pragma once
+
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#define XD_HD __host__ __device__ __forceinline__
+#else
+#define XD_HD inline
+#endif
+
+namespace xd {
+
+XD_HD int orb_ctz(uint64_t v) {
+#ifdef __CUDA_ARCH__
+    return __ffsll((long long)v) - 1;
+#else
+    return __builtin_ctzll(v);
+#endif
+}
+
+XD_HD int orb_popc(uint64_t v) {
+#ifdef __CUDA_ARCH__
+    return __popcll(v);
+#else
+    return __builtin_popcountll(v);
+#endif
+}
+
+struct TorusGeo {
+    int Lx, Ly, N;
+    uint32_t rowmask;       // 2^Lx - 1
+    uint64_t nmask;         // 2^N - 1
+    uint64_t rep1;          // bit 0 of every row
+    const uint16_t *rowtab; // [2^Lx]
+};
+
+XD_HD TorusGeo torus_geo(int Lx, int Ly, const uint16_t *rowtab) {
+    TorusGeo g;
+    g.Lx = Lx;
+    g.Ly = Ly;
+    g.N = Lx * Ly;
+    g.rowmask = (1u << Lx) - 1;
+    g.nmask = g.N == 64 ? ~0ull : ((1ull << g.N) - 1);
+    g.rep1 = 0;
+    for (int y = 0; y < Ly; ++y) g.rep1 |= 1ull << (Lx * y);
+    g.rowtab = rowtab;
+    return g;
+}
+
+XD_HD uint32_t torus_row(const TorusGeo &g, uint64_t w, int y) {
+    return (uint32_t)(w >> (g.Lx * y)) & g.rowmask;
+}
+
+// T_{a,b} w on the whole word: the rows move down by b, every row rotates by a.
+XD_HD uint64_t torus_translate(const TorusGeo &g, uint64_t w, int a, int b) {
+    if (b) w = ((w >> (g.Lx * b)) | (w << (g.N - g.Lx * b))) & g.nmask;
+    if (a) {
+        const uint64_t low = g.rep1 * ((1ull << (g.Lx - a)) - 1);  // bits that move down by a
+        w = ((w >> a) & low) | ((w << (g.Lx - a)) & (g.nmask ^ low));
+    }
+    return w;
+}
+
+// Smallest top row over the translations of w (*top) and the candidates
+// reaching it: the row y that comes to the top under T_{a,b} has b = (y + 1) mod Ly.
+XD_HD uint64_t torus_top(const TorusGeo &g, uint64_t w, uint32_t *top) {
+    uint32_t best = 0xffffffffu;
+    uint64_t M = 0;
+    for (int y = 0; y < g.Ly; ++y) {
+        const uint32_t e = g.rowtab[torus_row(g, w, y)];
+        const uint32_t v = e & 0xffu;
+        const int b = y + 1 == g.Ly ? 0 : y + 1;
+        const uint64_t bits = (uint64_t)(e >> 8) << (8 * b);
+        if (v < best) {
+            best = v;
+            M = bits;
+        } else if (v == best) {
+            M |= bits;
+        }
+    }
+    *top = best;
+    return M;
+}
+
+// Narrows the candidates M (all with top row `top`) of w to those reaching the
+// smallest image *img.  With bounded set the search stops, returning false,
+// as soon as the image is known to exceed bound.
+XD_HD bool torus_narrow(const TorusGeo &g, uint64_t w, uint32_t top, uint64_t &M, bool bounded,
+                        uint64_t bound, uint64_t *img_out) {
+    const int ytop = g.Ly - 1;
+    uint64_t img = (uint64_t)top << (g.Lx * ytop);
+    bool tight = bounded && torus_row(g, bound, ytop) == top;  // image prefix == bound prefix
+    for (int y = ytop - 1; y >= 0; --y) {
+        if ((M & (M - 1)) == 0) {  // one candidate: its image in one go
+            const int q = orb_ctz(M);
+            *img_out = torus_translate(g, w, q & 7, q >> 3);
+            return !(tight && *img_out > bound);
+        }
+        uint32_t vmin = 0xffffffffu;
+        uint64_t M2 = 0, bm = M;
+        while (bm) {
+            const int b = orb_ctz(bm) >> 3;
+            uint32_t am = (uint32_t)(bm >> (8 * b)) & 0xffu;
+            bm &= ~(0xffull << (8 * b));
+            int ys = y + b;
+            if (ys >= g.Ly) ys -= g.Ly;
+            const uint32_t r = torus_row(g, w, ys);
+            while (am) {
+                const int a = orb_ctz(am);
+                am &= am - 1;
+                const uint32_t v = a ? (((r >> a) | (r << (g.Lx - a))) & g.rowmask) : r;
+                const uint64_t bit = 1ull << (a + 8 * b);
+                if (v < vmin) {
+                    vmin = v;
+                    M2 = bit;
+                } else if (v == vmin) {
+                    M2 |= bit;
+                }
+            }
+        }
+        M = M2;
+        img |= (uint64_t)vmin << (g.Lx * y);
+        if (tight) {
+            const uint32_t br = torus_row(g, bound, y);
+            if (vmin > br) return false;
+            tight = vmin == br;
+        }
+    }
+    *img_out = img;
+    return true;
+}
+
+struct TorusOrbit {
+    uint64_t rep;  // smallest image
+    int k, q;      // a winning coset and translation (bit q = a + 8 b)
+    int cnt;       // number of (coset, translation) pairs reaching rep
+};
+
+// Smallest image of s over the union of ncos cosets; wk(k) returns p_k s.
+template <class W>
+XD_HD TorusOrbit torus_orbit(const TorusGeo &g, int ncos, W wk) {
+    TorusOrbit o{~0ull, 0, 0, 0};
+    uint32_t gbest = 0xffffffffu;  // top row of o.rep (o.cnt > 0)
+    for (int k = 0; k < ncos; ++k) {
+        const uint64_t w = wk(k);
+        uint32_t top;
+        uint64_t M = torus_top(g, w, &top);
+        if (o.cnt && top > gbest) continue;
+        const bool bounded = o.cnt && top == gbest;
+        uint64_t img;
+        if (!torus_narrow(g, w, top, M, bounded, o.rep, &img)) continue;
+        if (!bounded || img < o.rep) {
+            o.rep = img;
+            o.k = k;
+            o.q = orb_ctz(M);
+            o.cnt = orb_popc(M);
+            gbest = top;
+        } else if (img == o.rep) {
+            o.cnt += orb_popc(M);
+        }
+    }
+    return o;
+}
+
+}  // namespace xd

@@ -26,6 +26,7 @@
 
 #include "xd_groups.h"
 #include "xd_internal.cuh"
+#include "xd_orbit.h"
 
 namespace xd {
 
@@ -220,8 +221,39 @@ __device__ __forceinline__ Orbit orbit_min_ring(const SymView &v, uint64_t s) {
     return o;
 }
 
+// Narrowing search of xd_orbit.h (tori with at most 8 rows); rowtab in
+// global or shared memory.
+__device__ __forceinline__ TorusGeo torus_view(const SymView &v, const uint16_t *rowtab) {
+    TorusGeo g;
+    g.Lx = v.tx;
+    g.Ly = v.ty;
+    g.N = v.N;
+    g.rowmask = (1u << v.tx) - 1;
+    g.nmask = v.N == 64 ? ~0ull : ((1ull << v.N) - 1);
+    g.rep1 = v.trep1;
+    g.rowtab = rowtab;
+    return g;
+}
+
+__device__ __forceinline__ Orbit torus_result(const SymView &v, const TorusOrbit &t) {
+    Orbit o;
+    o.rep = t.rep;
+    o.cnt = t.cnt;
+    o.u = __ldg(v.tg + t.k * v.N + (t.q & 7) + v.tx * (t.q >> 3));
+    return o;
+}
+
+__device__ __forceinline__ Orbit orbit_min_narrow(const SymView &v, const TorusGeo &g, uint64_t s) {
+    return torus_result(v, torus_orbit(g, v.tnp ? v.tnp : 1, [&](int k) {
+                            return k ? act(v.act, v.nchunk, __ldg(v.tpp + k), s) : s;
+                        }));
+}
+
 __device__ __forceinline__ Orbit orbit_min(const SymView &v, uint64_t s) {
-    if (v.tx) return v.tnp ? orbit_min_cosets(v, s) : orbit_min_torus(v, s);
+    if (v.tx) {
+        if (v.ty <= 8) return orbit_min_narrow(v, torus_view(v, v.rowtab), s);
+        return v.tnp ? orbit_min_cosets(v, s) : orbit_min_torus(v, s);
+    }
     return v.cn ? orbit_min_ring(v, s) : orbit_min_tables(v, s);
 }
 
@@ -399,6 +431,7 @@ __global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, const double 
     double *sm_sq = sm_chi + 2 * v.G;       // [2 (G+1)]
     uint64_t *sm_pm = (uint64_t *)(sm_sq + 2 * (v.G + 1));  // COS: [tnp - 1][nb]
     uint64_t *sm_ps = sm_pm + (COS ? (v.tnp - 1) * nb : 0);   // COS: [tnp - 1][threads]
+    uint16_t *sm_rowtab = (uint16_t *)(sm_ps + (COS ? (v.tnp - 1) * kThreads : 0));  // [2^tx]
     const uint64_t *masks = (const uint64_t *)(bond + nb);
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         sm_half[b] = 0.5 * bond[b];
@@ -408,6 +441,10 @@ __global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, const double 
     for (int q = threadIdx.x; q < 2 * (v.G + 1); q += blockDim.x) sm_sq[q] = sq[q];
     if constexpr (COS)
         for (int q = threadIdx.x; q < (v.tnp - 1) * nb; q += blockDim.x) sm_pm[q] = v.pm[q];
+    const bool narrow = v.tx && v.ty <= 8;
+    if (narrow)
+        for (int q = threadIdx.x; q < (1 << v.tx); q += blockDim.x) sm_rowtab[q] = v.rowtab[q];
+    const TorusGeo tgeo = torus_view(v, sm_rowtab);
     const double jq = bond[2 * nb];
     __syncthreads();
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < v.dim;
@@ -427,11 +464,12 @@ __global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, const double 
             dsub += hb;
             Orbit o;
             if constexpr (COS) {
-                o = coset_search(v, [&](int k) {
+                auto wk = [&](int k) {
                     return k ? sm_ps[(k - 1) * kThreads + threadIdx.x] ^ sm_pm[(k - 1) * nb + b] : s ^ mk;
-                });
+                };
+                o = narrow ? torus_result(v, torus_orbit(tgeo, v.tnp, wk)) : coset_search(v, wk);
             } else {
-                o = orbit_min(v, s ^ mk);
+                o = narrow ? orbit_min_narrow(v, tgeo, s ^ mk) : orbit_min(v, s ^ mk);
             }
             const int64_t k = __ldg(v.u1.hi_off + (o.rep >> v.u1.L)) +
                               (int64_t)__ldg(v.u1.lo_rank + (o.rep & v.u1.lomask));
@@ -568,6 +606,10 @@ static xd_status make_tables(xd_basis_s *b) {
     if (T.tx) {
         XD_TRY(upload(&b->d_minrot, T.minrot));
         XD_TRY(upload(&b->d_amask, T.amask));
+        std::vector<uint16_t> rowtab(T.minrot.size());
+        for (size_t r = 0; r < rowtab.size(); ++r) rowtab[r] = (uint16_t)(T.minrot[r] | (T.amask[r] << 8));
+        XD_TRY(upload(&b->d_rowtab, rowtab));
+        b->trep1 = torus_geo(T.tx, T.ty, nullptr).rep1;
         XD_TRY(upload(&b->d_tg, T.tg));
         XD_TRY(upload(&b->d_tpp, T.tpp));
         if (T.tnp) XD_TRY(upload(&b->d_pm, T.pm));
@@ -685,7 +727,8 @@ xd_status sym_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, cuda
     SymWork w;
     XD_TRY(sym_work(h, 0, &w));
     const SymView v = b->symview();
-    size_t smem = (size_t)nb * 16 + 2 * G * sizeof(double) + 2 * (size_t)(G + 1) * sizeof(double);
+    size_t smem = (size_t)nb * 16 + 2 * G * sizeof(double) + 2 * (size_t)(G + 1) * sizeof(double) +
+                  256 * sizeof(uint16_t);  // row table of the narrowing search
     const size_t smem_cos = smem + (size_t)std::max(0, b->tnp - 1) * (nb + kThreads) * sizeof(uint64_t);
     int optin = 0;
     {

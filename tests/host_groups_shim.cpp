@@ -25,3 +25,32 @@ extern "C" void shim_group_tables(int N, int G, const int32_t *perms, const int3
     for (size_t i = 0; i < T.pm.size(); ++i) pm[i] = T.pm[i];
     for (size_t i = 0; i < T.cg.size(); ++i) cg[i] = T.cg[i];
 }
+
+// Representative search of xd_orbit.h on n words: rep, |Stab| (pairs of coset
+// and translation reaching rep) and the group index of one element reaching
+// it.  Returns 0 when the group is not a torus with Ly <= 8.
+#include <vector>
+#include "xd_orbit.h"
+
+extern "C" int shim_torus_orbit(int N, int G, const int32_t *perms, const int32_t *bonds, int nb, int64_t n,
+                                const uint64_t *s, uint64_t *rep, int32_t *cnt, int32_t *u) {
+    xd::GroupTables T;
+    xd::group_tables(N, G, perms, bonds, nb, &T);
+    if (!T.tx || T.ty > 8) return 0;
+    std::vector<uint16_t> rowtab(1u << T.tx);
+    for (size_t r = 0; r < rowtab.size(); ++r) rowtab[r] = (uint16_t)(T.minrot[r] | (T.amask[r] << 8));
+    const xd::TorusGeo g = xd::torus_geo(T.tx, T.ty, rowtab.data());
+    auto act = [&](int e, uint64_t w) {
+        uint64_t r = 0;
+        for (int c = 0; c < T.nchunk; ++c) r |= T.act[((size_t)e * T.nchunk + c) * 256 + ((w >> (8 * c)) & 255)];
+        return r;
+    };
+    const int ncos = T.tnp ? T.tnp : 1;
+    for (int64_t i = 0; i < n; ++i) {
+        const xd::TorusOrbit o = xd::torus_orbit(g, ncos, [&](int k) { return k ? act(T.tpp[k], s[i]) : s[i]; });
+        rep[i] = o.rep;
+        cnt[i] = o.cnt;
+        u[i] = T.tg[(size_t)o.k * N + (o.q & 7) + T.tx * (o.q >> 3)];
+    }
+    return 1;
+}

@@ -62,3 +62,43 @@ def test_batch_c4_shapes(orc):
         for v in (0, 7):
             yo = orc.apply_rows_rng(d["N"], d["nup"], d["bonds"], d["J"], 1000 * k + v, rows)
             assert rel_l2(ys[k][torch.from_numpy(rows).cuda(), v].double().cpu().numpy(), yo) < 5e-6
+
+
+def test_batch_fused_mixed_and_new_couplings(orc):
+    """Eight FP32 columns, large (N = 24, prefix blocks) and small operators in
+    the one fused launch; after new couplings on a large and a small operator
+    the next call uses them (the captured launch is rebuilt)."""
+    A = api()
+    insts = W.batched_instances(count=7, seed=9, sizes=(12, 14, 24))
+    assert {d["N"] for d in insts} >= {24, 12}
+    hams, xs, ys = [], [], []
+    for k, d in enumerate(insts):
+        ham = A.Hamiltonian(A.Basis(d["N"], d["nup"], d["bonds"]), d["J"])
+        x = torch.stack([A.random_vector(ham.dim, 500 * k + v, torch.float64) for v in range(8)], 1)
+        hams.append(ham)
+        xs.append(x.float().contiguous())
+        ys.append(torch.empty_like(xs[-1]))
+    rng = np.random.default_rng(2)
+
+    def check(Js):
+        for y in ys:
+            y.zero_()
+        A.batch_apply(hams, xs, ys)
+        torch.cuda.synchronize()
+        for k, d in enumerate(insts):
+            rows = np.unique(np.concatenate([[0, hams[k].dim - 1], rng.integers(0, hams[k].dim, 48)]))
+            for v in (0, 3, 7):
+                yo = orc.apply_rows_rng(d["N"], d["nup"], d["bonds"], Js[k], 500 * k + v, rows)
+                got = ys[k][torch.from_numpy(rows).cuda(), v].double().cpu().numpy()
+                assert rel_l2(got, yo) < 5e-6, (k, d["N"], v)
+
+    Js = [d["J"] for d in insts]
+    check(Js)
+    check(Js)  # graph replay
+    big = next(k for k, d in enumerate(insts) if d["N"] == 24)
+    small = next(k for k, d in enumerate(insts) if d["N"] < 24)
+    for k in (big, small):
+        Js[k] = 1.7 * Js[k] - 0.4
+        hams[k].set_couplings(Js[k])
+    check(Js)
+    check(Js)

@@ -203,3 +203,73 @@ def test_group_tables(shim, case):
             assert perms[cg[n]].tolist() == [(i + n) % N for i in range(N)]
             if m["cdih"]:
                 assert perms[cg[N + n]].tolist() == [(n - i) % N for i in range(N)]
+
+
+def _brute_rep(perms, words):
+    """Smallest image over every group element, |Stab|, by the definition
+    (g s)_i = s_{g(i)}."""
+    G, N = perms.shape
+    bits = ((words[:, None] >> np.arange(N, dtype=np.uint64)) & np.uint64(1)).astype(np.uint64)
+    img = np.zeros((len(words), G), dtype=np.uint64)
+    for g in range(G):
+        img[:, g] = (bits[:, perms[g]] << np.arange(N, dtype=np.uint64)).sum(axis=1, dtype=np.uint64)
+    rep = img.min(axis=1)
+    return rep, (img == rep[:, None]).sum(axis=1), img
+
+
+def _apply_perm(perm, w):
+    N = len(perm)
+    return sum(((int(w) >> int(perm[i])) & 1) << i for i in range(N))
+
+
+TORUS_CASES = [
+    ("6x6 translations", W.torus_translations(6, 6), W.square_j1j2(6, 6)[0], 18),
+    ("6x6 square space group", W.space_group(6, 6, "square"), W.square_j1j2(6, 6)[0], 18),
+    ("6x6 triangular space group", W.space_group(6, 6, "triangular"), W.triangular(6)[0], 17),
+    ("4x4 square space group", W.space_group(4, 4, "square"), W.square_j1j2(4, 4)[0], 8),
+    ("8x8 translations", W.torus_translations(8, 8), W.square_j1j2(8, 8)[0], 32),
+    ("3x5 translations", W.torus_translations(3, 5), W.square_j1j2(3, 5)[0], 7),
+]
+
+
+@pytest.mark.parametrize("case", range(len(TORUS_CASES)))
+def test_torus_narrowing_search_matches_every_element(shim, case):
+    """The row-by-row narrowing search (xd_orbit.h) returns the smallest image
+    over every group element, the stabiliser size, and an element reaching
+    it, on random words, periodic words (many equal candidates) and the
+    all-zero / all-one words."""
+    name, perms, bonds, nup = TORUS_CASES[case]
+    perms = np.ascontiguousarray(perms, dtype=np.int32)
+    bonds = np.ascontiguousarray(bonds, dtype=np.int32)
+    G, N = perms.shape
+    rng = np.random.default_rng(11 + case)
+    words = []
+    for _ in range(3000):
+        sites = rng.choice(N, size=int(rng.integers(0, N + 1)) if _ % 3 == 0 else nup, replace=False)
+        words.append(sum(1 << int(i) for i in sites))
+    # words invariant under translations: stripes and checkerboards of the torus
+    Lx = {"6x6": 6, "4x4": 4, "8x8": 8, "3x5": 3}[name.split()[0]]
+    Ly = N // Lx
+    for pat in (0b01, 0b011, 0b0101, 0b0011):
+        row = sum(((pat >> (x % 4)) & 1) << x for x in range(Lx))
+        words.append(sum(row << (Lx * y) for y in range(Ly)))
+        words.append(sum((row if y % 2 else (~row & ((1 << Lx) - 1))) << (Lx * y) for y in range(Ly)))
+    words += [0, (1 << N) - 1]
+    words = np.array(words, dtype=np.uint64)
+    n = len(words)
+    rep = np.zeros(n, np.uint64)
+    cnt = np.zeros(n, np.int32)
+    u = np.zeros(n, np.int32)
+    P = ctypes.POINTER
+    shim.shim_torus_orbit.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_int32), ctypes.c_int,
+                                      ctypes.c_int64, P(ctypes.c_uint64), P(ctypes.c_uint64), P(ctypes.c_int32),
+                                      P(ctypes.c_int32)]
+    ok = shim.shim_torus_orbit(N, G, _p(perms, ctypes.c_int32), _p(bonds, ctypes.c_int32), len(bonds), n,
+                               _p(words, ctypes.c_uint64), _p(rep, ctypes.c_uint64), _p(cnt, ctypes.c_int32),
+                               _p(u, ctypes.c_int32))
+    assert ok == 1, name
+    brep, bcnt, img = _brute_rep(perms, words)
+    np.testing.assert_array_equal(rep, brep)
+    np.testing.assert_array_equal(cnt, bcnt)
+    np.testing.assert_array_equal(img[np.arange(n), u], brep)
+    assert bcnt.max() > 1  # the periodic words exercise equal candidates
