@@ -224,6 +224,8 @@ static void free_basis(xd_basis_s *b) {
     cudaFree(b->d_minrot);
     cudaFree(b->d_amask);
     cudaFree(b->d_rowtab);
+    cudaFree(b->d_cut);
+    cudaFree(b->d_krow);
     cudaFree(b->d_tg);
     cudaFree(b->d_tpp);
     cudaFree(b->d_pm);
@@ -265,6 +267,8 @@ xd::SymView xd_basis_s::symview() const {
     v.minrot = d_minrot;
     v.amask = d_amask;
     v.rowtab = d_rowtab;
+    v.cut = d_cut;
+    v.krow = d_krow;
     v.trep1 = trep1;
     v.tg = d_tg;
     v.tnp = tnp;

@@ -89,7 +89,8 @@ inline int couplings_invariant(int N, int G, const int32_t *perms, const int32_t
 //   tg[k Lx Ly + a + Lx b] = group index of s -> T_{a,b}(p_k s), whose site
 //   map is i -> p_k(T_{a,b}(i)); tnp = number of cosets, 0 when only the
 //   translations; minrot[r] / amask[r] = smallest rotation of an Lx-bit row
-//   and the rotations reaching it; pm[(k - 1) nb + q] = p_k applied to the
+//   and the rotations reaching it; cut (Lx <= 7) = the same over a subset of
+//   the rotations (xd_orbit.h); pm[(k - 1) nb + q] = p_k applied to the
 //   mask of bond q (k >= 1).
 //   Ring (only without a torus): the group is the N rotations i -> i + n,
 //   with or without the N reflections i -> n - i (mod N); cg[n] and
@@ -99,6 +100,7 @@ struct GroupTables {
     std::vector<uint64_t> act;
     int tx = 0, ty = 0, tnp = 0;
     std::vector<uint8_t> minrot, amask;
+    std::vector<uint16_t> cut;  // Lx <= 7: cut[(r << Lx) | A] (xd_orbit.h)
     std::vector<int16_t> tg, tpp;
     std::vector<uint64_t> pm;
     int cn = 0, cdih = 0;
@@ -175,6 +177,24 @@ inline void group_tables(int N, int G, const int32_t *perms, const int32_t *bond
             }
             T.minrot[r] = (uint8_t)m;
             T.amask[r] = (uint8_t)mask;
+        }
+        if (Lx <= 7) {
+            T.cut.assign((size_t)1 << (2 * Lx), 0);
+            for (uint32_t r = 0; r < (1u << Lx); ++r)
+                for (uint32_t A = 1; A < (1u << Lx); ++A) {
+                    uint32_t m = 0xffu, sub = 0;
+                    for (int a = 0; a < Lx; ++a) {
+                        if (!((A >> a) & 1)) continue;
+                        const uint32_t rr = ((r >> a) | (r << (Lx - a))) & ((1u << Lx) - 1);
+                        if (rr < m) {
+                            m = rr;
+                            sub = 1u << a;
+                        } else if (rr == m) {
+                            sub |= 1u << a;
+                        }
+                    }
+                    T.cut[((size_t)r << Lx) | A] = (uint16_t)(m | (sub << 8));
+                }
         }
         T.tx = Lx;
         T.ty = Ly;

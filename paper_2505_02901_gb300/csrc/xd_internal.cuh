@@ -75,8 +75,11 @@ struct SymView {
     // element s -> T_{a,b}(p_k s).  tnp = 0: translations only.
     int tx, ty, tnp;
     const uint8_t *minrot, *amask;
-    // rowtab[r] = minrot[r] | amask[r] << 8; trep1 = bit 0 of every row
-    const uint16_t *rowtab;
+    // rowtab[r] = minrot[r] | amask[r] << 8; trep1 = bit 0 of every row;
+    // cut: the narrowing search's row table (tx <= 7, else null; xd_orbit.h);
+    // krow[k nb + b] = the rows of the two sites of p_k applied to bond b
+    // (low byte, high byte), k < max(1, tnp), p_0 the identity
+    const uint16_t *rowtab, *cut, *krow;
     uint64_t trep1;
     const int16_t *tg, *tpp;
     // pm[(k - 1) nb + b] = p_k applied to the mask of bond b (k >= 1): the
@@ -166,7 +169,7 @@ struct xd_basis_s {
     int nchunk = 0;
     int tx = 0, ty = 0, tnp = 0;     // detected torus translations (and their cosets)
     uint8_t *d_minrot = nullptr, *d_amask = nullptr;
-    uint16_t *d_rowtab = nullptr;
+    uint16_t *d_rowtab = nullptr, *d_cut = nullptr, *d_krow = nullptr;
     uint64_t trep1 = 0;
     int16_t *d_tg = nullptr, *d_tpp = nullptr;
     uint64_t *d_pm = nullptr;        // point images of the bond masks

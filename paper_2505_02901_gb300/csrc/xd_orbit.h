@@ -15,7 +15,10 @@
 //
 // Candidates are the bits a + 8 b of a 64-bit word (Lx <= 8, Ly <= 8).
 // Tables: rowtab[r] = smallest rotation of the Lx-bit row r (low byte) and
-// the mask of the rotations a reaching it (high byte).
+// the mask of the rotations a reaching it (high byte); cut[(r << Lx) | A]
+// (Lx <= 7, optional) = the smallest rot_a(r) over a in the mask A (low byte)
+// and the a in A reaching it (high byte), so that one row step of a
+// candidate b costs one lookup however many rotations it still holds.
 
 #pragma once
 
@@ -51,18 +54,20 @@ struct TorusGeo {
     uint64_t nmask;         // 2^N - 1
     uint64_t rep1;          // bit 0 of every row
     const uint16_t *rowtab; // [2^Lx]
+    const uint16_t *cut;    // [2^(2 Lx)] or null
 };
 
-XD_HD TorusGeo torus_geo(int Lx, int Ly, const uint16_t *rowtab) {
+XD_HD TorusGeo torus_geo(int Lx, int Ly, const uint16_t *rowtab, const uint16_t *cut = nullptr) {
     TorusGeo g;
     g.Lx = Lx;
     g.Ly = Ly;
     g.N = Lx * Ly;
     g.rowmask = (1u << Lx) - 1;
-    g.nmask = g.N == 64 ? ~0ull : ((1ull << g.N) - 1);
+    g.nmask = ~0ull >> (64 - g.N);
     g.rep1 = 0;
     for (int y = 0; y < Ly; ++y) g.rep1 |= 1ull << (Lx * y);
     g.rowtab = rowtab;
+    g.cut = cut;
     return g;
 }
 
@@ -72,12 +77,10 @@ XD_HD uint32_t torus_row(const TorusGeo &g, uint64_t w, int y) {
 
 // T_{a,b} w on the whole word: the rows move down by b, every row rotates by a.
 XD_HD uint64_t torus_translate(const TorusGeo &g, uint64_t w, int a, int b) {
-    if (b) w = ((w >> (g.Lx * b)) | (w << (g.N - g.Lx * b))) & g.nmask;
-    if (a) {
-        const uint64_t low = g.rep1 * ((1ull << (g.Lx - a)) - 1);  // bits that move down by a
-        w = ((w >> a) & low) | ((w << (g.Lx - a)) & (g.nmask ^ low));
-    }
-    return w;
+    const int sb = g.Lx * b;  // every shift below stays under 64
+    w = ((w >> sb) | (w << ((g.N - sb) & 63))) & g.nmask;
+    const uint64_t low = g.rep1 * ((1ull << (g.Lx - a)) - 1);  // bits that move down by a
+    return ((w >> a) & low) | ((w << (g.Lx - a)) & (g.nmask ^ low));
 }
 
 // Smallest top row over the translations of w (*top) and the candidates
@@ -124,17 +127,32 @@ XD_HD bool torus_narrow(const TorusGeo &g, uint64_t w, uint32_t top, uint64_t &M
             int ys = y + b;
             if (ys >= g.Ly) ys -= g.Ly;
             const uint32_t r = torus_row(g, w, ys);
-            while (am) {
-                const int a = orb_ctz(am);
-                am &= am - 1;
-                const uint32_t v = a ? (((r >> a) | (r << (g.Lx - a))) & g.rowmask) : r;
-                const uint64_t bit = 1ull << (a + 8 * b);
-                if (v < vmin) {
-                    vmin = v;
-                    M2 = bit;
-                } else if (v == vmin) {
-                    M2 |= bit;
+            uint32_t v, sub;
+            if (g.cut) {
+                const uint32_t e = g.cut[(r << g.Lx) | am];
+                v = e & 0xffu;
+                sub = e >> 8;
+            } else {
+                v = 0xffffffffu;
+                sub = 0;
+                while (am) {
+                    const int a = orb_ctz(am);
+                    am &= am - 1;
+                    const uint32_t va = a ? (((r >> a) | (r << (g.Lx - a))) & g.rowmask) : r;
+                    if (va < v) {
+                        v = va;
+                        sub = 1u << a;
+                    } else if (va == v) {
+                        sub |= 1u << a;
+                    }
                 }
+            }
+            const uint64_t bits = (uint64_t)sub << (8 * b);
+            if (v < vmin) {
+                vmin = v;
+                M2 = bits;
+            } else if (v == vmin) {
+                M2 |= bits;
             }
         }
         M = M2;
@@ -149,21 +167,75 @@ XD_HD bool torus_narrow(const TorusGeo &g, uint64_t w, uint32_t top, uint64_t &M
     return true;
 }
 
+// Row state of a word for the top step: byte y of PM = smallest rotation of
+// row y, byte y of PA = the rotations reaching it (bytes y >= Ly: 0xff / 0).
+// A flip changes one or two rows; torus_rows_set refreshes row y from the
+// flipped word, and torus_top_rows gives what torus_top gives, by byte-wise
+// minimum and comparison.
+XD_HD uint32_t bytes_min8(uint64_t v) {
+#ifdef __CUDA_ARCH__
+    uint32_t m = __vminu4((uint32_t)v, (uint32_t)(v >> 32));
+    m = __vminu4(m, m >> 16);
+    m = __vminu4(m, m >> 8);
+    return m & 0xffu;
+#else
+    uint32_t m = 0xffu;
+    for (int q = 0; q < 8; ++q) m = ((v >> (8 * q)) & 0xffu) < m ? (uint32_t)((v >> (8 * q)) & 0xffu) : m;
+    return m;
+#endif
+}
+
+// 0xff in every byte of v equal to the byte t, 0 elsewhere
+XD_HD uint64_t bytes_eq8(uint64_t v, uint32_t t) {
+#ifdef __CUDA_ARCH__
+    const uint32_t tt = t * 0x01010101u;
+    return (uint64_t)__vcmpeq4((uint32_t)v, tt) | ((uint64_t)__vcmpeq4((uint32_t)(v >> 32), tt) << 32);
+#else
+    uint64_t r = 0;
+    for (int q = 0; q < 8; ++q)
+        if (((v >> (8 * q)) & 0xffu) == t) r |= 0xffull << (8 * q);
+    return r;
+#endif
+}
+
+XD_HD void torus_rows_set(const TorusGeo &g, uint64_t &PM, uint64_t &PA, uint64_t w, int y) {
+    const uint32_t e = g.rowtab[torus_row(g, w, y)];
+    const uint64_t keep = ~(0xffull << (8 * y));
+    PM = (PM & keep) | ((uint64_t)(e & 0xffu) << (8 * y));
+    PA = (PA & keep) | ((uint64_t)(e >> 8) << (8 * y));
+}
+
+XD_HD void torus_rows(const TorusGeo &g, uint64_t w, uint64_t &PM, uint64_t &PA) {
+    PM = ~0ull;
+    PA = 0;
+    for (int y = 0; y < g.Ly; ++y) torus_rows_set(g, PM, PA, w, y);
+}
+
+XD_HD uint64_t torus_top_rows(const TorusGeo &g, uint64_t PM, uint64_t PA, uint32_t *top) {
+    const uint32_t best = bytes_min8(PM);
+    const uint64_t Mr = bytes_eq8(PM, best) & PA;  // byte y: rotations of row y reaching best
+    *top = best;
+    // row y comes to the top under b = (y + 1) mod Ly
+    const int sh = 8 * (g.Ly - 1);
+    return ((Mr << 8) | (Mr >> sh)) & (~0ull >> (64 - 8 * g.Ly));
+}
+
 struct TorusOrbit {
     uint64_t rep;  // smallest image
     int k, q;      // a winning coset and translation (bit q = a + 8 b)
     int cnt;       // number of (coset, translation) pairs reaching rep
 };
 
-// Smallest image of s over the union of ncos cosets; wk(k) returns p_k s.
+// Smallest image of s over the union of ncos cosets; wk(k, &w, &top)
+// returns p_k s in w, its top row in top and the candidates reaching it.
 template <class W>
-XD_HD TorusOrbit torus_orbit(const TorusGeo &g, int ncos, W wk) {
+XD_HD TorusOrbit torus_orbit_top(const TorusGeo &g, int ncos, W wk) {
     TorusOrbit o{~0ull, 0, 0, 0};
     uint32_t gbest = 0xffffffffu;  // top row of o.rep (o.cnt > 0)
     for (int k = 0; k < ncos; ++k) {
-        const uint64_t w = wk(k);
+        uint64_t w;
         uint32_t top;
-        uint64_t M = torus_top(g, w, &top);
+        uint64_t M = wk(k, &w, &top);
         if (o.cnt && top > gbest) continue;
         const bool bounded = o.cnt && top == gbest;
         uint64_t img;
@@ -179,6 +251,15 @@ XD_HD TorusOrbit torus_orbit(const TorusGeo &g, int ncos, W wk) {
         }
     }
     return o;
+}
+
+// The same with wk(k) returning p_k s (top step from the word).
+template <class W>
+XD_HD TorusOrbit torus_orbit(const TorusGeo &g, int ncos, W wk) {
+    return torus_orbit_top(g, ncos, [&](int k, uint64_t *w, uint32_t *top) {
+        *w = wk(k);
+        return torus_top(g, *w, top);
+    });
 }
 
 }  // namespace xd

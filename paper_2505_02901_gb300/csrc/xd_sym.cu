@@ -223,15 +223,16 @@ __device__ __forceinline__ Orbit orbit_min_ring(const SymView &v, uint64_t s) {
 
 // Narrowing search of xd_orbit.h (tori with at most 8 rows); rowtab in
 // global or shared memory.
-__device__ __forceinline__ TorusGeo torus_view(const SymView &v, const uint16_t *rowtab) {
+__device__ __forceinline__ TorusGeo torus_view(const SymView &v, const uint16_t *rowtab, const uint16_t *cut) {
     TorusGeo g;
     g.Lx = v.tx;
     g.Ly = v.ty;
     g.N = v.N;
     g.rowmask = (1u << v.tx) - 1;
-    g.nmask = v.N == 64 ? ~0ull : ((1ull << v.N) - 1);
+    g.nmask = ~0ull >> (64 - v.N);
     g.rep1 = v.trep1;
     g.rowtab = rowtab;
+    g.cut = cut;
     return g;
 }
 
@@ -251,7 +252,7 @@ __device__ __forceinline__ Orbit orbit_min_narrow(const SymView &v, const TorusG
 
 __device__ __forceinline__ Orbit orbit_min(const SymView &v, uint64_t s) {
     if (v.tx) {
-        if (v.ty <= 8) return orbit_min_narrow(v, torus_view(v, v.rowtab), s);
+        if (v.ty <= 8) return orbit_min_narrow(v, torus_view(v, v.rowtab, v.cut), s);
         return v.tnp ? orbit_min_cosets(v, s) : orbit_min_torus(v, s);
     }
     return v.cn ? orbit_min_ring(v, s) : orbit_min_tables(v, s);
@@ -431,7 +432,10 @@ __global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, const double 
     double *sm_sq = sm_chi + 2 * v.G;       // [2 (G+1)]
     uint64_t *sm_pm = (uint64_t *)(sm_sq + 2 * (v.G + 1));  // COS: [tnp - 1][nb]
     uint64_t *sm_ps = sm_pm + (COS ? (v.tnp - 1) * nb : 0);   // COS: [tnp - 1][threads]
-    uint16_t *sm_rowtab = (uint16_t *)(sm_ps + (COS ? (v.tnp - 1) * kThreads : 0));  // [2^tx]
+    uint64_t *sm_st = sm_ps + (COS ? (v.tnp - 1) * kThreads : 0);  // COS: [tnp - 1][threads] row states
+    uint16_t *sm_rowtab = (uint16_t *)(sm_st + (COS ? 2 * (v.tnp - 1) * kThreads : 0));  // [256]
+    uint16_t *sm_cut = sm_rowtab + 256;                            // [2^(2 tx)] when v.cut
+    uint16_t *sm_krow = sm_cut + (v.cut ? (1 << (2 * v.tx)) : 0);  // [max(1, tnp)][nb] when narrow
     const uint64_t *masks = (const uint64_t *)(bond + nb);
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         sm_half[b] = 0.5 * bond[b];
@@ -442,49 +446,94 @@ __global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, const double 
     if constexpr (COS)
         for (int q = threadIdx.x; q < (v.tnp - 1) * nb; q += blockDim.x) sm_pm[q] = v.pm[q];
     const bool narrow = v.tx && v.ty <= 8;
-    if (narrow)
+    if (narrow) {
         for (int q = threadIdx.x; q < (1 << v.tx); q += blockDim.x) sm_rowtab[q] = v.rowtab[q];
-    const TorusGeo tgeo = torus_view(v, sm_rowtab);
+        if (v.cut)
+            for (int q = threadIdx.x; q < (1 << (2 * v.tx)); q += blockDim.x) sm_cut[q] = v.cut[q];
+        for (int q = threadIdx.x; q < max(1, v.tnp) * nb; q += blockDim.x) sm_krow[q] = v.krow[q];
+    }
+    // incremental top step (row states): translations alone, or the coset form
+    const bool rows = narrow && (COS || v.tnp == 0);
+    const TorusGeo tgeo = torus_view(v, sm_rowtab, v.cut ? sm_cut : nullptr);
     const double jq = bond[2 * nb];
     __syncthreads();
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < v.dim;
          r += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t s = __ldg(v.reps + r);
         const double isr = sm_sq[v.G + 1 + __ldg(v.stab + r)];
+        uint64_t PM = 0, PA = 0;  // row state of s
+        if (rows) torus_rows(tgeo, s, PM, PA);
         if constexpr (COS) {
-            for (int k = 1; k < v.tnp; ++k)
-                sm_ps[(k - 1) * kThreads + threadIdx.x] = act(v.act, v.nchunk, __ldg(v.tpp + k), s);
+            for (int k = 1; k < v.tnp; ++k) {
+                const uint64_t w = act(v.act, v.nchunk, __ldg(v.tpp + k), s);
+                sm_ps[(k - 1) * kThreads + threadIdx.x] = w;
+                if (rows) {
+                    uint64_t pm, pa;
+                    torus_rows(tgeo, w, pm, pa);
+                    sm_st[2 * ((k - 1) * kThreads + threadIdx.x)] = pm;
+                    sm_st[2 * ((k - 1) * kThreads + threadIdx.x) + 1] = pa;
+                }
+            }
         }
         double ar = 0.0, ai = 0.0, dsub = 0.0;
-        for (int b = 0; b < nb; ++b) {
-            const uint64_t mk = sm_mask[b];
-            const uint64_t t = s & mk;
-            if (t == 0 || t == mk) continue;
-            const double hb = sm_half[b];
-            dsub += hb;
-            Orbit o;
-            if constexpr (COS) {
-                auto wk = [&](int k) {
-                    return k ? sm_ps[(k - 1) * kThreads + threadIdx.x] ^ sm_pm[(k - 1) * nb + b] : s ^ mk;
-                };
-                o = narrow ? torus_result(v, torus_orbit(tgeo, v.tnp, wk)) : coset_search(v, wk);
-            } else {
-                o = narrow ? orbit_min_narrow(v, tgeo, s ^ mk) : orbit_min(v, s ^ mk);
+        // bonds in chunks of 64: the flipping ones of a chunk (antiparallel
+        // sites) as the set bits of F, so that a warp takes as many steps as
+        // its rows have flips rather than one per bond
+        for (int b0 = 0; b0 < nb; b0 += 64) {
+            const int nq = min(64, nb - b0);
+            uint64_t F = 0;
+            for (int q = 0; q < nq; ++q) {
+                const uint64_t mq = sm_mask[b0 + q];
+                const uint64_t t = s & mq;
+                F |= (uint64_t)(t != 0 && t != mq) << q;
             }
-            const int64_t k = __ldg(v.u1.hi_off + (o.rep >> v.u1.L)) +
-                              (int64_t)__ldg(v.u1.lo_rank + (o.rep & v.u1.lomask));
-            const ulonglong2 wc = __ldg(v.rs + (k >> 6));
-            const uint64_t word = wc.x;
-            if (!((word >> (k & 63)) & 1)) continue;
-            const int64_t c = (int64_t)wc.y + __popcll(word & ((1ull << (k & 63)) - 1));
-            const double a = hb * sm_sq[o.cnt] * isr;
-            if constexpr (CPLX) {
-                const double2 xc = x[c];
-                const double cr = a * sm_chi[2 * o.u], ci = a * sm_chi[2 * o.u + 1];
-                ar += cr * xc.x - ci * xc.y;
-                ai += cr * xc.y + ci * xc.x;
-            } else {
-                ar += a * sm_chi[2 * o.u] * x[c];
+            while (F) {
+                const int b = b0 + __ffsll((long long)F) - 1;
+                F &= F - 1;
+                const uint64_t mk = sm_mask[b];
+                const double hb = sm_half[b];
+                dsub += hb;
+                Orbit o;
+                if (rows) {
+                    // p_k of the flipped word, its row state refreshed in the two rows of the flip
+                    o = torus_result(v, torus_orbit_top(tgeo, COS ? v.tnp : 1,
+                                                        [&](int k, uint64_t *w, uint32_t *top) {
+                        uint64_t pm = PM, pa = PA;
+                        if (COS && k) {
+                            const int e = (k - 1) * kThreads + threadIdx.x;
+                            *w = sm_ps[e] ^ sm_pm[(k - 1) * nb + b];
+                            pm = sm_st[2 * e];
+                            pa = sm_st[2 * e + 1];
+                        } else {
+                            *w = s ^ mk;
+                        }
+                        const uint32_t rr = sm_krow[k * nb + b];
+                        torus_rows_set(tgeo, pm, pa, *w, rr & 0xffu);
+                        torus_rows_set(tgeo, pm, pa, *w, rr >> 8);
+                        return torus_top_rows(tgeo, pm, pa, top);
+                    }));
+                } else if constexpr (COS) {
+                    o = coset_search(v, [&](int k) {
+                        return k ? sm_ps[(k - 1) * kThreads + threadIdx.x] ^ sm_pm[(k - 1) * nb + b] : s ^ mk;
+                    });
+                } else {
+                    o = narrow ? orbit_min_narrow(v, tgeo, s ^ mk) : orbit_min(v, s ^ mk);
+                }
+                const int64_t k = __ldg(v.u1.hi_off + (o.rep >> v.u1.L)) +
+                                  (int64_t)__ldg(v.u1.lo_rank + (o.rep & v.u1.lomask));
+                const ulonglong2 wc = __ldg(v.rs + (k >> 6));
+                const uint64_t word = wc.x;
+                if (!((word >> (k & 63)) & 1)) continue;
+                const int64_t c = (int64_t)wc.y + __popcll(word & ((1ull << (k & 63)) - 1));
+                const double a = hb * sm_sq[o.cnt] * isr;
+                if constexpr (CPLX) {
+                    const double2 xc = x[c];
+                    const double cr = a * sm_chi[2 * o.u], ci = a * sm_chi[2 * o.u + 1];
+                    ar += cr * xc.x - ci * xc.y;
+                    ai += cr * xc.y + ci * xc.x;
+                } else {
+                    ar += a * sm_chi[2 * o.u] * x[c];
+                }
             }
         }
         const double d = jq - dsub;
@@ -609,6 +658,17 @@ static xd_status make_tables(xd_basis_s *b) {
         std::vector<uint16_t> rowtab(T.minrot.size());
         for (size_t r = 0; r < rowtab.size(); ++r) rowtab[r] = (uint16_t)(T.minrot[r] | (T.amask[r] << 8));
         XD_TRY(upload(&b->d_rowtab, rowtab));
+        if (!T.cut.empty()) XD_TRY(upload(&b->d_cut, T.cut));
+        const int ncos = std::max(1, T.tnp), nb = b->nb;
+        std::vector<uint16_t> krow((size_t)ncos * nb);
+        for (int k = 0; k < ncos; ++k)
+            for (int q = 0; q < nb; ++q) {
+                const uint64_t m = k ? T.pm[(size_t)(k - 1) * nb + q]
+                                     : (1ull << b->bonds[q].i) | (1ull << b->bonds[q].j);
+                const int lo = __builtin_ctzll(m) / T.tx, hi = (63 - __builtin_clzll(m)) / T.tx;
+                krow[(size_t)k * nb + q] = (uint16_t)(lo | (hi << 8));
+            }
+        XD_TRY(upload(&b->d_krow, krow));
         b->trep1 = torus_geo(T.tx, T.ty, nullptr).rep1;
         XD_TRY(upload(&b->d_tg, T.tg));
         XD_TRY(upload(&b->d_tpp, T.tpp));
@@ -727,9 +787,12 @@ xd_status sym_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, cuda
     SymWork w;
     XD_TRY(sym_work(h, 0, &w));
     const SymView v = b->symview();
-    size_t smem = (size_t)nb * 16 + 2 * G * sizeof(double) + 2 * (size_t)(G + 1) * sizeof(double) +
-                  256 * sizeof(uint16_t);  // row table of the narrowing search
-    const size_t smem_cos = smem + (size_t)std::max(0, b->tnp - 1) * (nb + kThreads) * sizeof(uint64_t);
+    // row tables of the narrowing search, the bonds' rows
+    const size_t tabs = (256 + (b->d_cut ? ((size_t)1 << (2 * b->tx)) : 0) + (size_t)std::max(1, b->tnp) * nb) *
+                        sizeof(uint16_t);
+    size_t smem = (size_t)nb * 16 + 2 * G * sizeof(double) + 2 * (size_t)(G + 1) * sizeof(double) + tabs;
+    // coset form: point images of the bond masks, per-thread images of the row and their row states
+    const size_t smem_cos = smem + (size_t)std::max(0, b->tnp - 1) * (nb + 3 * kThreads) * sizeof(uint64_t);
     int optin = 0;
     {
         int dev = 0;
@@ -743,7 +806,7 @@ xd_status sym_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, cuda
     }
     int grid = grid_for(v.dim, kThreads, 8);
     // coset form when the point images of the bond masks fit beside the rest
-    const bool cos = v.tx && v.tnp > 1 && v.tnp <= kMaxCos && smem_cos <= std::min<size_t>(optin, 96 * 1024);
+    const bool cos = v.tx && v.tnp > 1 && v.tnp <= kMaxCos && smem_cos <= (size_t)optin;
     if (cos) smem = smem_cos;
     if (dt == XD_C128) {
         auto kern = cos ? k_sym_apply<true, true> : k_sym_apply<true, false>;

@@ -28,18 +28,20 @@ extern "C" void shim_group_tables(int N, int G, const int32_t *perms, const int3
 
 // Representative search of xd_orbit.h on n words: rep, |Stab| (pairs of coset
 // and translation reaching rep) and the group index of one element reaching
-// it.  Returns 0 when the group is not a torus with Ly <= 8.
+// it, with or without the cut table.  Returns 0 when the group is not a torus
+// with Ly <= 8 (or the cut table was asked for and Lx > 7).
 #include <vector>
 #include "xd_orbit.h"
 
 extern "C" int shim_torus_orbit(int N, int G, const int32_t *perms, const int32_t *bonds, int nb, int64_t n,
-                                const uint64_t *s, uint64_t *rep, int32_t *cnt, int32_t *u) {
+                                const uint64_t *s, uint64_t *rep, int32_t *cnt, int32_t *u, int use_cut) {
     xd::GroupTables T;
     xd::group_tables(N, G, perms, bonds, nb, &T);
     if (!T.tx || T.ty > 8) return 0;
     std::vector<uint16_t> rowtab(1u << T.tx);
     for (size_t r = 0; r < rowtab.size(); ++r) rowtab[r] = (uint16_t)(T.minrot[r] | (T.amask[r] << 8));
-    const xd::TorusGeo g = xd::torus_geo(T.tx, T.ty, rowtab.data());
+    if (use_cut && T.cut.empty()) return 0;
+    const xd::TorusGeo g = xd::torus_geo(T.tx, T.ty, rowtab.data(), use_cut ? T.cut.data() : nullptr);
     auto act = [&](int e, uint64_t w) {
         uint64_t r = 0;
         for (int c = 0; c < T.nchunk; ++c) r |= T.act[((size_t)e * T.nchunk + c) * 256 + ((w >> (8 * c)) & 255)];
@@ -53,4 +55,31 @@ extern "C" int shim_torus_orbit(int N, int G, const int32_t *perms, const int32_
         u[i] = T.tg[(size_t)o.k * N + (o.q & 7) + T.tx * (o.q >> 3)];
     }
     return 1;
+}
+
+// Incremental top step (xd_orbit.h): the row state of s refreshed in the rows
+// of sites i and j against the top step of s ^ (bit i | bit j) computed from
+// the word; returns the number of words where top row or candidates differ.
+extern "C" int64_t shim_top_rows_mismatch(int N, int G, const int32_t *perms, const int32_t *bonds, int nb,
+                                          int64_t n, const uint64_t *s, const int32_t *ij) {
+    xd::GroupTables T;
+    xd::group_tables(N, G, perms, bonds, nb, &T);
+    if (!T.tx || T.ty > 8) return -1;
+    std::vector<uint16_t> rowtab(1u << T.tx);
+    for (size_t r = 0; r < rowtab.size(); ++r) rowtab[r] = (uint16_t)(T.minrot[r] | (T.amask[r] << 8));
+    const xd::TorusGeo g = xd::torus_geo(T.tx, T.ty, rowtab.data());
+    int64_t bad = 0;
+    for (int64_t q = 0; q < n; ++q) {
+        uint64_t PM, PA;
+        xd::torus_rows(g, s[q], PM, PA);
+        const int i = ij[2 * q], j = ij[2 * q + 1];
+        const uint64_t w = s[q] ^ (1ull << i) ^ (1ull << j);
+        xd::torus_rows_set(g, PM, PA, w, i / T.tx);
+        xd::torus_rows_set(g, PM, PA, w, j / T.tx);
+        uint32_t t1, t2;
+        const uint64_t M1 = xd::torus_top_rows(g, PM, PA, &t1);
+        const uint64_t M2 = xd::torus_top(g, w, &t2);
+        bad += (t1 != t2 || M1 != M2);
+    }
+    return bad;
 }
