@@ -470,6 +470,7 @@ static xd_status set_J(xd_ham_s *h, const double *J) {
     buf[2 * b->nb] = 0.25 * q;
     XD_CUDA(cudaMemcpy(h->d_bond, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice));
     if (b->sym && !h->d_symtab) XD_TRY(sym_ham_tables(h));
+    if (b->sym) XD_TRY(sym_bond_groups(h));
     if (b->blk.ok) XD_TRY(block_ham_tables(h));
     if (b->spmm.ok) XD_TRY(spmm_ham_tables(h));
     if (b->spmm.ok) XD_TRY(passes_tables(h));
@@ -520,6 +521,7 @@ void xd_ham_destroy(xd_ham h) {
     cudaFree(h->d_bond);
     cudaFree(h->d_lzpart);
     cudaFree(h->d_symtab);
+    cudaFree(h->d_symgrp);
     cudaFree(h->d_dpost);
     cudaFree(h->d_sp_dpost);
     cudaFree(h->d_sp_jhalf);

@@ -195,6 +195,11 @@ struct xd_ham_s {
     double *d_lzpart = nullptr;     // Lanczos reduction partials
     int lzpart_n = 0;
     double *d_symtab = nullptr;     // symmetric blocks: sqrt(a), 1/sqrt(a) [G+1 each] | bond orbit ids
+    // symmetric blocks: bonds sorted by coupling, in chunks of 64 split into
+    // groups of equal coupling (sym_bond_groups): [nb] masks | [ngrp] group
+    // masks | [ngrp] J/2 | [nb] u16 bond ids | [nchunk + 1] u16 first groups
+    uint64_t *d_symgrp = nullptr;
+    int sym_ngrp = 0;
     double *d_dpost = nullptr;      // block layout: postfix diagonal per L-bit word
     float *d_sp_dpost = nullptr;    // batched layout: postfix diagonal per class position
     float *d_sp_jhalf = nullptr;    // batched layout: J/2 per bond
@@ -237,6 +242,7 @@ xd_status u1_bilinear_nvec(const xd_ham_s *h, const void *g, const void *x, xd_d
 // symmetric blocks (xd_sym.cu)
 xd_status sym_build(xd_basis_s *b);
 xd_status sym_ham_tables(xd_ham_s *h);
+xd_status sym_bond_groups(xd_ham_s *h);  // on every new set of couplings
 xd_status sym_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt,
                     cudaStream_t st);
 xd_status sym_bilinear(const xd_ham_s *h, const void *g, const void *x,

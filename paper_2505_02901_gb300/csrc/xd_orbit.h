@@ -167,35 +167,34 @@ XD_HD bool torus_narrow(const TorusGeo &g, uint64_t w, uint32_t top, uint64_t &M
     return true;
 }
 
-// Row state of a word for the top step: byte y of PM = smallest rotation of
-// row y, byte y of PA = the rotations reaching it (bytes y >= Ly: 0xff / 0).
+// Row state of a word for the top step (rows of at most 7 sites): byte y of
+// PM = smallest rotation of row y, byte y of PA = the rotations reaching it
+// (bytes y >= Ly: 0x7f / 0, above every row value and never a candidate).
 // A flip changes one or two rows; torus_rows_set refreshes row y from the
 // flipped word, and torus_top_rows gives what torus_top gives, by byte-wise
-// minimum and comparison.
+// minimum and comparison on plain integer operations (every byte < 128).
+XD_HD uint32_t bytes_min4(uint32_t a, uint32_t b) {
+    const uint32_t ge = ((a | 0x80808080u) - b) & 0x80808080u;  // 0x80 where a >= b
+    const uint32_t sel = (ge >> 7) * 0xffu;
+    return (b & sel) | (a & ~sel);
+}
+
 XD_HD uint32_t bytes_min8(uint64_t v) {
-#ifdef __CUDA_ARCH__
-    uint32_t m = __vminu4((uint32_t)v, (uint32_t)(v >> 32));
-    m = __vminu4(m, m >> 16);
-    m = __vminu4(m, m >> 8);
+    uint32_t m = bytes_min4((uint32_t)v, (uint32_t)(v >> 32));
+    m = bytes_min4(m, m >> 16);
+    m = bytes_min4(m, m >> 8);
     return m & 0xffu;
-#else
-    uint32_t m = 0xffu;
-    for (int q = 0; q < 8; ++q) m = ((v >> (8 * q)) & 0xffu) < m ? (uint32_t)((v >> (8 * q)) & 0xffu) : m;
-    return m;
-#endif
 }
 
 // 0xff in every byte of v equal to the byte t, 0 elsewhere
+XD_HD uint32_t bytes_eq4(uint32_t v, uint32_t t) {
+    const uint32_t x = v ^ (t * 0x01010101u);  // zero bytes where equal
+    const uint32_t z = ~(((x & 0x7f7f7f7fu) + 0x7f7f7f7fu) | x | 0x7f7f7f7fu);  // 0x80 in zero bytes
+    return (z >> 7) * 0xffu;
+}
+
 XD_HD uint64_t bytes_eq8(uint64_t v, uint32_t t) {
-#ifdef __CUDA_ARCH__
-    const uint32_t tt = t * 0x01010101u;
-    return (uint64_t)__vcmpeq4((uint32_t)v, tt) | ((uint64_t)__vcmpeq4((uint32_t)(v >> 32), tt) << 32);
-#else
-    uint64_t r = 0;
-    for (int q = 0; q < 8; ++q)
-        if (((v >> (8 * q)) & 0xffu) == t) r |= 0xffull << (8 * q);
-    return r;
-#endif
+    return (uint64_t)bytes_eq4((uint32_t)v, t) | ((uint64_t)bytes_eq4((uint32_t)(v >> 32), t) << 32);
 }
 
 XD_HD void torus_rows_set(const TorusGeo &g, uint64_t &PM, uint64_t &PA, uint64_t w, int y) {
@@ -206,7 +205,7 @@ XD_HD void torus_rows_set(const TorusGeo &g, uint64_t &PM, uint64_t &PA, uint64_
 }
 
 XD_HD void torus_rows(const TorusGeo &g, uint64_t w, uint64_t &PM, uint64_t &PA) {
-    PM = ~0ull;
+    PM = 0x7f7f7f7f7f7f7f7full;
     PA = 0;
     for (int y = 0; y < g.Ly; ++y) torus_rows_set(g, PM, PA, w, y);
 }

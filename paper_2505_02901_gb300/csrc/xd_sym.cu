@@ -419,28 +419,65 @@ struct Val<true> {
 // with the point images of the bond masks (kept in shared memory).
 constexpr int kMaxCos = 12;
 
+// Bonds of the product sorted by coupling, in chunks of 64 (bit q of chunk c
+// is sorted bond 64 c + q); a group is a run of equal coupling inside one
+// chunk (the layout of xd_ham_s::d_symgrp).
+struct SymBonds {
+    const uint64_t *smask;  // [nb] site masks, sorted order
+    const uint64_t *gmask;  // [ngrp] bits of the group in its chunk
+    const double *ghalf;    // [ngrp] J/2
+    const uint16_t *perm;   // [nb] bond id of each sorted bond
+    const uint16_t *goff;   // [nchunk + 1] first group of each chunk
+    int ngrp, nchunk;
+};
+
+__host__ __device__ inline size_t symgrp_words(int nb, int ngrp) {
+    const int nchunk = (nb + 63) / 64;
+    return (size_t)nb + 2 * (size_t)ngrp + ((size_t)nb + nchunk + 1 + 3) / 4;
+}
+
+__host__ __device__ inline SymBonds symgrp_view(const uint64_t *base, int nb, int ngrp) {
+    SymBonds v;
+    v.smask = base;
+    v.gmask = base + nb;
+    v.ghalf = (const double *)(base + nb + ngrp);
+    v.perm = (const uint16_t *)(base + nb + 2 * ngrp);
+    v.goff = v.perm + nb;
+    v.ngrp = ngrp;
+    v.nchunk = (nb + 63) / 64;
+    return v;
+}
+
 template <bool CPLX, bool COS>
-__global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, const double *__restrict__ bond,
-                                                        int nb, const double *__restrict__ chi,
+__global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, SymBonds sbo, int nb, double jq,
+                                                        const double *__restrict__ chi,
                                                         const double *__restrict__ sq,
                                                         const typename Val<CPLX>::T *__restrict__ x,
                                                         typename Val<CPLX>::T *__restrict__ y) {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t *sm_mask = (uint64_t *)smem;
-    double *sm_half = (double *)(sm_mask + nb);
-    double *sm_chi = sm_half + nb;          // [G][2]
-    double *sm_sq = sm_chi + 2 * v.G;       // [2 (G+1)]
+    const int ngrp = sbo.ngrp, nchunk = sbo.nchunk;
+    uint64_t *sm_smask = (uint64_t *)smem;                   // [nb] sorted bonds
+    uint64_t *sm_gmask = sm_smask + nb;                      // [ngrp]
+    double *sm_ghalf = (double *)(sm_gmask + ngrp);          // [ngrp]
+    double *sm_chi = sm_ghalf + ngrp;                        // [G][2]
+    double *sm_sq = sm_chi + 2 * v.G;                        // [2 (G+1)]
     uint64_t *sm_pm = (uint64_t *)(sm_sq + 2 * (v.G + 1));  // COS: [tnp - 1][nb]
     uint64_t *sm_ps = sm_pm + (COS ? (v.tnp - 1) * nb : 0);   // COS: [tnp - 1][threads]
     uint64_t *sm_st = sm_ps + (COS ? (v.tnp - 1) * kThreads : 0);  // COS: [tnp - 1][threads] row states
     uint16_t *sm_rowtab = (uint16_t *)(sm_st + (COS ? 2 * (v.tnp - 1) * kThreads : 0));  // [256]
     uint16_t *sm_cut = sm_rowtab + 256;                            // [2^(2 tx)] when v.cut
-    uint16_t *sm_krow = sm_cut + (v.cut ? (1 << (2 * v.tx)) : 0);  // [max(1, tnp)][nb] when narrow
-    const uint64_t *masks = (const uint64_t *)(bond + nb);
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        sm_half[b] = 0.5 * bond[b];
-        sm_mask[b] = masks[b];
+    uint16_t *sm_krow = sm_cut + (v.cut ? (1 << (2 * v.tx)) : 0);  // [max(1, tnp)][nb]
+    uint16_t *sm_perm = sm_krow + max(1, v.tnp) * nb;              // [nb]
+    uint16_t *sm_goff = sm_perm + nb;                              // [nchunk + 1]
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) {
+        sm_smask[q] = sbo.smask[q];
+        sm_perm[q] = sbo.perm[q];
     }
+    for (int q = threadIdx.x; q < ngrp; q += blockDim.x) {
+        sm_gmask[q] = sbo.gmask[q];
+        sm_ghalf[q] = sbo.ghalf[q];
+    }
+    for (int q = threadIdx.x; q <= nchunk; q += blockDim.x) sm_goff[q] = sbo.goff[q];
     for (int g = threadIdx.x; g < 2 * v.G; g += blockDim.x) sm_chi[g] = chi[g];
     for (int q = threadIdx.x; q < 2 * (v.G + 1); q += blockDim.x) sm_sq[q] = sq[q];
     if constexpr (COS)
@@ -452,15 +489,14 @@ __global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, const double 
             for (int q = threadIdx.x; q < (1 << (2 * v.tx)); q += blockDim.x) sm_cut[q] = v.cut[q];
         for (int q = threadIdx.x; q < max(1, v.tnp) * nb; q += blockDim.x) sm_krow[q] = v.krow[q];
     }
-    // incremental top step (row states): translations alone, or the coset form
-    const bool rows = narrow && (COS || v.tnp == 0);
+    // incremental top step (row states, rows of at most 7 sites): translations
+    // alone, or the coset form
+    const bool rows = narrow && v.tx <= 7 && (COS || v.tnp == 0);
     const TorusGeo tgeo = torus_view(v, sm_rowtab, v.cut ? sm_cut : nullptr);
-    const double jq = bond[2 * nb];
     __syncthreads();
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < v.dim;
          r += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t s = __ldg(v.reps + r);
-        const double isr = sm_sq[v.G + 1 + __ldg(v.stab + r)];
         uint64_t PM = 0, PA = 0;  // row state of s
         if (rows) torus_rows(tgeo, s, PM, PA);
         if constexpr (COS) {
@@ -475,73 +511,83 @@ __global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, const double 
                 }
             }
         }
+        // sum over flips of sqrt(|Stab(r')|) chi(u) x_{r'}, per group of equal
+        // coupling, times J/2; 1/sqrt(|Stab(r)|) once at the end
         double ar = 0.0, ai = 0.0, dsub = 0.0;
-        // bonds in chunks of 64: the flipping ones of a chunk (antiparallel
-        // sites) as the set bits of F, so that a warp takes as many steps as
-        // its rows have flips rather than one per bond
-        for (int b0 = 0; b0 < nb; b0 += 64) {
-            const int nq = min(64, nb - b0);
+        for (int ch = 0; ch < nchunk; ++ch) {
+            const int b0 = 64 * ch, nq = min(64, nb - b0);
+            // flipping bonds of the chunk (antiparallel sites) as the set bits
+            // of F, so that a warp takes as many steps as its rows have flips
             uint64_t F = 0;
             for (int q = 0; q < nq; ++q) {
-                const uint64_t mq = sm_mask[b0 + q];
+                const uint64_t mq = sm_smask[b0 + q];
                 const uint64_t t = s & mq;
                 F |= (uint64_t)(t != 0 && t != mq) << q;
             }
-            while (F) {
-                const int b = b0 + __ffsll((long long)F) - 1;
-                F &= F - 1;
-                const uint64_t mk = sm_mask[b];
-                const double hb = sm_half[b];
-                dsub += hb;
-                Orbit o;
-                if (rows) {
-                    // p_k of the flipped word, its row state refreshed in the two rows of the flip
-                    o = torus_result(v, torus_orbit_top(tgeo, COS ? v.tnp : 1,
-                                                        [&](int k, uint64_t *w, uint32_t *top) {
-                        uint64_t pm = PM, pa = PA;
-                        if (COS && k) {
-                            const int e = (k - 1) * kThreads + threadIdx.x;
-                            *w = sm_ps[e] ^ sm_pm[(k - 1) * nb + b];
-                            pm = sm_st[2 * e];
-                            pa = sm_st[2 * e + 1];
-                        } else {
-                            *w = s ^ mk;
-                        }
-                        const uint32_t rr = sm_krow[k * nb + b];
-                        torus_rows_set(tgeo, pm, pa, *w, rr & 0xffu);
-                        torus_rows_set(tgeo, pm, pa, *w, rr >> 8);
-                        return torus_top_rows(tgeo, pm, pa, top);
-                    }));
-                } else if constexpr (COS) {
-                    o = coset_search(v, [&](int k) {
-                        return k ? sm_ps[(k - 1) * kThreads + threadIdx.x] ^ sm_pm[(k - 1) * nb + b] : s ^ mk;
-                    });
-                } else {
-                    o = narrow ? orbit_min_narrow(v, tgeo, s ^ mk) : orbit_min(v, s ^ mk);
+            for (int g = sm_goff[ch]; g < sm_goff[ch + 1]; ++g) {
+                uint64_t Fg = F & sm_gmask[g];
+                const double hb = sm_ghalf[g];
+                dsub += hb * __popcll(Fg);
+                double gr = 0.0, gi = 0.0;
+                while (Fg) {
+                    const int bs = b0 + __ffsll((long long)Fg) - 1;
+                    Fg &= Fg - 1;
+                    const uint64_t mk = sm_smask[bs];
+                    const int b = sm_perm[bs];  // bond id (point-image and row tables)
+                    Orbit o;
+                    if (rows) {
+                        // p_k of the flipped word, its row state refreshed in the two rows of the flip
+                        o = torus_result(v, torus_orbit_top(tgeo, COS ? v.tnp : 1,
+                                                            [&](int k, uint64_t *w, uint32_t *top) {
+                            uint64_t pm = PM, pa = PA;
+                            if (COS && k) {
+                                const int e = (k - 1) * kThreads + threadIdx.x;
+                                *w = sm_ps[e] ^ sm_pm[(k - 1) * nb + b];
+                                pm = sm_st[2 * e];
+                                pa = sm_st[2 * e + 1];
+                            } else {
+                                *w = s ^ mk;
+                            }
+                            const uint32_t rr = sm_krow[k * nb + b];
+                            torus_rows_set(tgeo, pm, pa, *w, rr & 0xffu);
+                            torus_rows_set(tgeo, pm, pa, *w, rr >> 8);
+                            return torus_top_rows(tgeo, pm, pa, top);
+                        }));
+                    } else if constexpr (COS) {
+                        o = coset_search(v, [&](int k) {
+                            return k ? sm_ps[(k - 1) * kThreads + threadIdx.x] ^ sm_pm[(k - 1) * nb + b] : s ^ mk;
+                        });
+                    } else {
+                        o = narrow ? orbit_min_narrow(v, tgeo, s ^ mk) : orbit_min(v, s ^ mk);
+                    }
+                    const int64_t k = __ldg(v.u1.hi_off + (o.rep >> v.u1.L)) +
+                                      (int64_t)__ldg(v.u1.lo_rank + (o.rep & v.u1.lomask));
+                    const ulonglong2 wc = __ldg(v.rs + (k >> 6));
+                    const uint64_t word = wc.x;
+                    if (!((word >> (k & 63)) & 1)) continue;
+                    const int64_t c = (int64_t)wc.y + __popcll(word & ((1ull << (k & 63)) - 1));
+                    const double a = sm_sq[o.cnt];
+                    if constexpr (CPLX) {
+                        const double2 xc = x[c];
+                        const double tr = a * xc.x, ti = a * xc.y;
+                        const double chr = sm_chi[2 * o.u], chim = sm_chi[2 * o.u + 1];
+                        gr += chr * tr - chim * ti;
+                        gi += chr * ti + chim * tr;
+                    } else {
+                        gr = fma(a * sm_chi[2 * o.u], x[c], gr);
+                    }
                 }
-                const int64_t k = __ldg(v.u1.hi_off + (o.rep >> v.u1.L)) +
-                                  (int64_t)__ldg(v.u1.lo_rank + (o.rep & v.u1.lomask));
-                const ulonglong2 wc = __ldg(v.rs + (k >> 6));
-                const uint64_t word = wc.x;
-                if (!((word >> (k & 63)) & 1)) continue;
-                const int64_t c = (int64_t)wc.y + __popcll(word & ((1ull << (k & 63)) - 1));
-                const double a = hb * sm_sq[o.cnt] * isr;
-                if constexpr (CPLX) {
-                    const double2 xc = x[c];
-                    const double cr = a * sm_chi[2 * o.u], ci = a * sm_chi[2 * o.u + 1];
-                    ar += cr * xc.x - ci * xc.y;
-                    ai += cr * xc.y + ci * xc.x;
-                } else {
-                    ar += a * sm_chi[2 * o.u] * x[c];
-                }
+                ar = fma(hb, gr, ar);
+                ai = fma(hb, gi, ai);
             }
         }
         const double d = jq - dsub;
+        const double isr = sm_sq[v.G + 1 + __ldg(v.stab + r)];
         if constexpr (CPLX) {
             const double2 xr = x[r];
-            y[r] = make_double2(d * xr.x + ar, d * xr.y + ai);
+            y[r] = make_double2(d * xr.x + isr * ar, d * xr.y + isr * ai);
         } else {
-            y[r] = d * x[r] + ar;
+            y[r] = d * x[r] + isr * ar;
         }
     }
 }
@@ -762,6 +808,52 @@ xd_status sym_ham_tables(xd_ham_s *h) {
     return XD_OK;
 }
 
+xd_status sym_bond_groups(xd_ham_s *h) {
+    const xd_basis_s *b = h->b;
+    const int nb = b->nb, nchunk = (nb + 63) / 64;
+    if (nb > 65535) {
+        set_error("symmetric product: %d bonds (at most 65535)", nb);
+        return XD_ERANGE;
+    }
+    std::vector<int> order(nb);
+    for (int q = 0; q < nb; ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return h->J[p] < h->J[q]; });
+    std::vector<uint64_t> gmask;
+    std::vector<double> ghalf;
+    std::vector<uint16_t> goff(nchunk + 1, 0);
+    for (int c = 0; c < nchunk; ++c) {
+        goff[c] = (uint16_t)gmask.size();
+        for (int q = 64 * c; q < std::min(nb, 64 * c + 64); ++q) {
+            const double J = h->J[order[q]];
+            if (q == 64 * c || J != h->J[order[q - 1]]) {
+                gmask.push_back(0);
+                ghalf.push_back(0.5 * J);
+            }
+            gmask.back() |= 1ull << (q - 64 * c);
+        }
+    }
+    goff[nchunk] = (uint16_t)gmask.size();
+    const int ngrp = (int)gmask.size();
+    std::vector<uint64_t> tab(symgrp_words(nb, ngrp), 0);
+    for (int q = 0; q < nb; ++q)
+        tab[q] = (1ull << b->bonds[order[q]].i) | (1ull << b->bonds[order[q]].j);
+    for (int g = 0; g < ngrp; ++g) {
+        tab[nb + g] = gmask[g];
+        memcpy(&tab[nb + ngrp + g], &ghalf[g], sizeof(double));
+    }
+    uint16_t *u16 = (uint16_t *)(tab.data() + nb + 2 * ngrp);
+    for (int q = 0; q < nb; ++q) u16[q] = (uint16_t)order[q];
+    for (int c = 0; c <= nchunk; ++c) u16[nb + c] = goff[c];
+    if (h->d_symgrp && h->sym_ngrp != ngrp) {
+        cudaFree(h->d_symgrp);
+        h->d_symgrp = nullptr;
+    }
+    if (!h->d_symgrp) XD_CUDA(dev_malloc((void **)&h->d_symgrp, tab.size() * sizeof(uint64_t)));
+    XD_CUDA(cudaMemcpy(h->d_symgrp, tab.data(), tab.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
+    h->sym_ngrp = ngrp;
+    return XD_OK;
+}
+
 struct SymWork {
     const double *sq;
     const int32_t *orbit;
@@ -787,10 +879,15 @@ xd_status sym_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, cuda
     SymWork w;
     XD_TRY(sym_work(h, 0, &w));
     const SymView v = b->symview();
-    // row tables of the narrowing search, the bonds' rows
-    const size_t tabs = (256 + (b->d_cut ? ((size_t)1 << (2 * b->tx)) : 0) + (size_t)std::max(1, b->tnp) * nb) *
-                        sizeof(uint16_t);
-    size_t smem = (size_t)nb * 16 + 2 * G * sizeof(double) + 2 * (size_t)(G + 1) * sizeof(double) + tabs;
+    const SymBonds sbo = symgrp_view(h->d_symgrp, nb, h->sym_ngrp);
+    double jq = 0.0;
+    for (int q = 0; q < nb; ++q) jq += h->J[q];
+    jq *= 0.25;
+    // u16 tables: rows of the narrowing search, the bonds' rows, bond ids, first groups
+    const size_t tabs = (256 + (b->d_cut ? ((size_t)1 << (2 * b->tx)) : 0) + (size_t)std::max(1, b->tnp) * nb + nb +
+                         sbo.nchunk + 1) * sizeof(uint16_t);
+    size_t smem = (size_t)nb * 8 + (size_t)sbo.ngrp * 16 + 2 * G * sizeof(double) +
+                  2 * (size_t)(G + 1) * sizeof(double) + tabs;
     // coset form: point images of the bond masks, per-thread images of the row and their row states
     const size_t smem_cos = smem + (size_t)std::max(0, b->tnp - 1) * (nb + 3 * kThreads) * sizeof(uint64_t);
     int optin = 0;
@@ -811,13 +908,11 @@ xd_status sym_apply(const xd_ham_s *h, const void *x, void *y, xd_dtype dt, cuda
     if (dt == XD_C128) {
         auto kern = cos ? k_sym_apply<true, true> : k_sym_apply<true, false>;
         XD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<grid, kThreads, smem, st>>>(v, h->d_bond, nb, b->d_chi, w.sq, (const double2 *)x,
-                                          (double2 *)y);
+        kern<<<grid, kThreads, smem, st>>>(v, sbo, nb, jq, b->d_chi, w.sq, (const double2 *)x, (double2 *)y);
     } else {
         auto kern = cos ? k_sym_apply<false, true> : k_sym_apply<false, false>;
         XD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<grid, kThreads, smem, st>>>(v, h->d_bond, nb, b->d_chi, w.sq, (const double *)x,
-                                          (double *)y);
+        kern<<<grid, kThreads, smem, st>>>(v, sbo, nb, jq, b->d_chi, w.sq, (const double *)x, (double *)y);
     }
     XD_CUDA(cudaGetLastError());
     return XD_OK;

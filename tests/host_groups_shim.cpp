@@ -65,6 +65,7 @@ extern "C" int64_t shim_top_rows_mismatch(int N, int G, const int32_t *perms, co
     xd::GroupTables T;
     xd::group_tables(N, G, perms, bonds, nb, &T);
     if (!T.tx || T.ty > 8) return -1;
+    if (T.tx > 7) return -2;  // row states hold rows of at most 7 sites
     std::vector<uint16_t> rowtab(1u << T.tx);
     for (size_t r = 0; r < rowtab.size(); ++r) rowtab[r] = (uint16_t)(T.minrot[r] | (T.amask[r] << 8));
     const xd::TorusGeo g = xd::torus_geo(T.tx, T.ty, rowtab.data());

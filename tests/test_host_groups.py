@@ -299,4 +299,7 @@ def test_torus_incremental_top_step(shim, case):
                                             ctypes.c_int, ctypes.c_int64, P(ctypes.c_uint64), P(ctypes.c_int32)]
     bad = shim.shim_top_rows_mismatch(N, G, _p(perms, ctypes.c_int32), _p(bonds, ctypes.c_int32), len(bonds),
                                       len(words), _p(words, ctypes.c_uint64), _p(ij, ctypes.c_int32))
+    if name.startswith("8x8"):
+        assert bad == -2  # rows of 8 sites take the search from the word
+        return
     assert bad == 0, name
