@@ -21,8 +21,11 @@
 #include <algorithm>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "xd_internal.cuh"
 #include "xd_tridiag.h"
+#include "xd_u1_rows.cuh"
 
 namespace xd {
 
@@ -90,6 +93,13 @@ struct AccOf<float> {
     using A = AccF;
 };
 
+// Vector updates with their roundings spelt out (a product, then one fused
+// multiply-add), so that every kernel forming a Lanczos vector -- the first
+// pass in any of its forms and the second pass that rebuilds the vectors
+// from the recorded alpha and beta -- rounds alike and the second pass
+// reproduces the first pass's vectors.
+// (mul_rn, fma_rn: xd_u1_rows.cuh)
+
 // block-wide sum of one double per thread into part[blockIdx.x] (fixed order)
 __device__ __forceinline__ void block_store(double v, double *__restrict__ part) {
     __shared__ double red[kThreads / 32];
@@ -114,8 +124,8 @@ __global__ void __launch_bounds__(kThreads) k_axpby_dot(int64_t n, T *__restrict
     typename AccOf<T>::A acc;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        T t = a * w[i];
-        if (z) t += c * z[i];
+        T t = mul_rn(a, w[i]);
+        if (z) t = fma_rn(c, z[i], t);
         w[i] = t;
         if (mode == 1) acc.add(t, v[i]);
         else if (mode == 2) acc.add(t, t);
@@ -225,7 +235,7 @@ __global__ void __launch_bounds__(kThreads) k_lz_axpby1(int64_t n, T *__restrict
     const T a = (T)sd->sig, c = (T)sd->cz;
     typename AccOf<T>::A acc;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const T t = a * w[i] + c * up[i];
+        const T t = fma_rn(c, up[i], mul_rn(a, w[i]));
         w[i] = t;
         acc.add(t, u[i]);
     }
@@ -248,7 +258,7 @@ __global__ void __launch_bounds__(kThreads) k_lz_axpby2(int64_t n, T *__restrict
     const T c = (T)sd->ca;
     typename AccOf<T>::A acc;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const T t = w[i] + c * u[i];
+        const T t = fma_rn(c, u[i], w[i]);
         w[i] = t;
         acc.add(t, t);
     }
@@ -265,6 +275,106 @@ __global__ void __launch_bounds__(kThreads) k_lz_axpby2(int64_t n, T *__restrict
             sd->cz = -bt * sd->sig;
             sd->sig = 1.0 / bt;
         }
+    }
+}
+
+// The whole first pass in one cooperative launch, for small U(1) blocks
+// whose product is the plain row loop, one row per thread: the row's state
+// word is unranked once and kept in a register.  A step is two phases
+// separated by grid-wide barriers:
+//   product: w_r = (H u)_r in the row loop's order and roundings
+//     (xd_u1_rows.cuh), so that the vectors are those of the second pass bit
+//     for bit, with the partial dots <H u, u> and <up, u>, so that
+//     alpha_k = sig <sig H u + cz up, u> (the modified form) needs no
+//     further pass;
+//   update: w = sig w + cz up - alpha_k sig u, with the partial norms.
+// Every CTA sums the partials itself in the fixed order of warp_sum_parts,
+// so all CTAs hold the same alpha, beta and stop decision; CTA 0 records
+// them.  A thread updates only its own row, so only the product's gathers
+// read other CTAs' writes (through L2).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_lz_persist(U1View u1, const double *__restrict__ bond, int nb,
+                                                         T *b0, T *b1, T *b2, LzDev *sd, double *pa,
+                                                         double *pb, double *pc, double *__restrict__ alpha,
+                                                         double *__restrict__ beta) {
+    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *sm_mask = (uint64_t *)smem;
+    T *sm_half = (T *)(sm_mask + nb);
+    __shared__ uint64_t sh_range[2];
+    __shared__ double sh_sum[2];
+    u1rows::stage_bonds(bond, nb, sm_mask, sm_half);
+    const T jq = (T)bond[2 * nb];
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // this thread's row
+    const u1rows::RowState rs = u1rows::unrank_tile(u1, (int64_t)blockIdx.x * blockDim.x, r, sh_range);
+    double sig = sd->sig, cz = sd->cz, amax = sd->amax;
+    int k = sd->k;
+    const int max_iter = sd->max_iter;
+    const bool rec = blockIdx.x == 0 && threadIdx.x == 0;
+    T *up = b0, *u = b1, *w = b2;
+    for (;;) {
+        double d1 = 0.0, d2 = 0.0;
+        if (rs.valid) {
+            T acc = T(0), dsub = T(0);
+            for (int b = 0; b < nb; ++b) {
+                const uint64_t mk = sm_mask[b];
+                const uint64_t t = rs.s & mk;
+                if (t != 0 && t != mk) {
+                    const T cf = sm_half[b];
+                    acc = fma_rn(cf, __ldcg(u + u1rows::rank_of(u1, rs.s ^ mk)), acc);
+                    dsub += cf;
+                }
+            }
+            const T ur = u[r];
+            const T wr = fma_rn(jq - dsub, ur, acc);
+            w[r] = wr;
+            d1 = (double)wr * (double)ur;
+            d2 = (double)up[r] * (double)ur;
+        }
+        block_store(d1, pa);
+        __syncthreads();  // thread 0 has read block_store's scratch before it is reused
+        block_store(d2, pb);
+        grid.sync();
+        if (threadIdx.x < 32) {
+            const double s1 = warp_sum_parts(pa, gridDim.x), s2 = warp_sum_parts(pb, gridDim.x);
+            if (threadIdx.x == 0) {
+                sh_sum[0] = s1;
+                sh_sum[1] = s2;
+            }
+        }
+        __syncthreads();
+        const double al = sig * (sig * sh_sum[0] + cz * sh_sum[1]);  // alpha_k
+        if (rec) alpha[k] = al;
+        amax = fmax(amax, fabs(al));
+        double d3 = 0.0;
+        if (rs.valid) {
+            const T t1 = fma_rn((T)cz, up[r], mul_rn((T)sig, w[r]));
+            const T t = fma_rn((T)(-al * sig), u[r], t1);
+            w[r] = t;
+            d3 = (double)t * (double)t;
+        }
+        block_store(d3, pc);
+        grid.sync();
+        if (threadIdx.x < 32) {
+            const double s3 = warp_sum_parts(pc, gridDim.x);
+            if (threadIdx.x == 0) sh_sum[0] = s3;
+        }
+        __syncthreads();
+        const double bt = sqrt(fmax(sh_sum[0], 0.0));  // beta_k = |w|
+        if (rec) beta[k] = bt;
+        k += 1;
+        if (!(bt > 0.0) || bt < 1e-13 * amax || k >= max_iter) break;  // the same in every CTA
+        cz = -bt * sig;
+        sig = 1.0 / bt;
+        T *t = up;
+        up = u;
+        u = w;
+        w = t;
+        __syncthreads();  // sh_sum read by every thread before the next step writes it
+    }
+    if (rec) {
+        sd->k = k;
+        sd->done = 1;
     }
 }
 
@@ -376,6 +486,36 @@ void lanczos_forget(xd_ham_s *h, bool all) {
     h->lz_ab_cap = 0;
 }
 
+// Launch shape of the cooperative first pass, or false where it does not
+// apply: a U(1) block without the block layouts (its product is the plain
+// row loop), one row per thread with every CTA resident, a device with
+// cooperative launch.
+struct LzSmall {
+    int grid;
+    size_t smem;
+};
+
+template <typename T>
+static bool lz_small_shape(const xd_ham_s *h, LzSmall *out) {
+    const xd_basis_s *b = h->b;
+    if (b->sym || b->blk.ok || b->spmm.ok || b->dim > (1 << 22)) return false;
+    int dev = 0, coop = 0, per_sm = 0;
+    const size_t smem = (size_t)b->nb * (sizeof(uint64_t) + sizeof(T));
+    if (smem > 48 * 1024 || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lz_persist<T>, kThreads, smem) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    grid_for(1, 1, 1);
+    const int64_t need = (b->dim + kThreads - 1) / kThreads;
+    if (need > (int64_t)per_sm * g_num_sms) return false;
+    out->grid = (int)need;
+    out->smem = smem;
+    return true;
+}
+
 template <typename T>
 static xd_status lanczos_pass1_graph(xd_ham_s *h, int max_iter, uint64_t seed, xd_dtype dt, double *alpha,
                                      double *beta, int *n_iter) {
@@ -385,10 +525,15 @@ static xd_status lanczos_pass1_graph(xd_ham_s *h, int max_iter, uint64_t seed, x
     const bool keep = 3 * vbytes <= kLzKeep;
     LzWork lw;
     lw.grid = grid_for(n, kThreads, 8);
-    XD_TRY(ensure_lanczos_partials(h, 2 * lw.grid));
+    // small blocks whose product is the plain row loop: one cooperative
+    // launch for the whole pass (all its CTAs resident at once)
+    LzSmall lzs{0, 0};
+    const bool persist = lz_small_shape<T>(h, &lzs);
+    const int pstride = std::max(lw.grid, lzs.grid);  // three arrays of partials
+    XD_TRY(ensure_lanczos_partials(h, 3 * pstride));
     lw.part = h->d_lzpart;
     lw.scal = h->d_scal;
-    double *part1 = h->d_lzpart, *part2 = h->d_lzpart + lw.grid;
+    double *part1 = h->d_lzpart, *part2 = h->d_lzpart + pstride;
     cudaError_t e = cudaSuccess;
     if (!h->lz_stream) e = cudaStreamCreateWithFlags(&h->lz_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess && !h->lz_dstate) e = dev_malloc(&h->lz_dstate, sizeof(LzDev));
@@ -409,6 +554,7 @@ static xd_status lanczos_pass1_graph(xd_ham_s *h, int max_iter, uint64_t seed, x
     const bool cached = h->lz_exec && h->lz_key_dt == (int)dt && h->lz_key_iter == max_iter;
     if (!cached) lanczos_forget(h, false);
     T *buf[3] = {(T *)h->lz_buf[0], (T *)h->lz_buf[1], (T *)h->lz_buf[2]};
+    double *d_abb = h->lz_ab + abcap;
     for (int k = 0; k < 3 && e == cudaSuccess; ++k)
         if (!buf[k]) e = dev_malloc_vec(h, (void **)&buf[k], std::max<size_t>(vbytes, 16));
     cudaGraph_t graph = nullptr;
@@ -434,7 +580,24 @@ static xd_status lanczos_pass1_graph(xd_ham_s *h, int max_iter, uint64_t seed, x
             rc = cuda_status(e, "Lanczos state");
             break;
         }
-        if (!exec) {
+        if (persist) {
+            // the whole pass in one cooperative launch
+            const int nbh = b->nb;
+            U1View u1 = b->u1view();
+            const double *bond = h->d_bond;
+            T *p0 = up, *p1 = u, *p2 = w;
+            double *part3 = h->d_lzpart + 2 * pstride;
+            void *args[] = {&u1, (void *)&bond, (void *)&nbh, &p0, &p1, &p2, &d_sd, &part1, &part2, &part3, &d_ab,
+                            (void *)&d_abb};
+            e = cudaLaunchCooperativeKernel((const void *)k_lz_persist<T>, dim3(lzs.grid), dim3(kThreads), args,
+                                            lzs.smem, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h_sd, d_sd, sizeof(LzDev), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) {
+                rc = cuda_status(e, "Lanczos (cooperative)");
+                break;
+            }
+        } else if (!exec) {
             // one product outside the capture (tables, workspaces)
             if ((rc = xd_apply(h, u, w, dt, 1, (xd_stream)st)) != XD_OK) break;
             if ((e = cudaStreamSynchronize(st)) != cudaSuccess) {
@@ -469,7 +632,7 @@ static xd_status lanczos_pass1_graph(xd_ham_s *h, int max_iter, uint64_t seed, x
             }
         }
         const int every = b->dim < (1 << 20) ? kLzCheckSmall : 1;
-        for (int rep = 0; e == cudaSuccess;) {
+        for (int rep = 0; !persist && e == cudaSuccess;) {
             e = cudaGraphLaunch(exec, st);
             if (e != cudaSuccess) break;
             if (++rep % every == 0 || 3 * rep >= max_iter) {

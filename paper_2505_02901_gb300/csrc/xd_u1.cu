@@ -13,6 +13,7 @@
 #include <mutex>
 
 #include "xd_internal.cuh"
+#include "xd_u1_rows.cuh"
 
 namespace xd {
 
@@ -20,65 +21,9 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// largest h in [lo, hi] with hi_off[h] <= r (hi_off is non-decreasing)
-__device__ __forceinline__ uint64_t find_block(const int64_t *__restrict__ hi_off, uint64_t lo,
-                                               uint64_t hi, int64_t r) {
-    while (lo < hi) {
-        uint64_t mid = (lo + hi + 1) >> 1;
-        if (__ldg(hi_off + mid) <= r) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
+using namespace u1rows;
 
-// Row r -> (state, block).  The CTA first brackets the blocks of its rows.
-struct RowState {
-    uint64_t s;
-    bool valid;
-};
-
-__device__ __forceinline__ RowState unrank_tile(const U1View &u, int64_t base, int64_t r,
-                                                uint64_t *sh_range) {
-    // sh_range[0..1]: block range of rows [base, base + blockDim.x)
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint64_t nh = 1ull << u.P;
-        int64_t last = min(base + (int64_t)blockDim.x, u.dim) - 1;
-        uint64_t h0 = find_block(u.hi_off, 0, nh - 1, base);
-        uint64_t h1 = find_block(u.hi_off, h0, nh - 1, last);
-        sh_range[0] = h0;
-        sh_range[1] = h1;
-    }
-    __syncthreads();
-    RowState rs;
-    rs.valid = r < u.dim;
-    rs.s = 0;
-    if (rs.valid) {
-        uint64_t h = find_block(u.hi_off, sh_range[0], sh_range[1], r);
-        int64_t i = r - __ldg(u.hi_off + h);
-        int m = u.nup - __popcll(h);
-        uint32_t l = __ldg(u.lo_list + __ldg(u.lo_off + m) + (uint32_t)i);
-        rs.s = (h << u.L) | l;
-    }
-    return rs;
-}
-
-__device__ __forceinline__ int64_t rank_of(const U1View &u, uint64_t t) {
-    return __ldg(u.hi_off + (t >> u.L)) + (int64_t)__ldg(u.lo_rank + (t & u.lomask));
-}
-
-template <typename T, int NV>
-struct Vec {
-    T v[NV];
-};
-
-template <typename T, int NV>
-__device__ __forceinline__ void load_row(const T *__restrict__ x, int64_t c, T (&out)[NV]) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) out[k] = __ldg(x + c * NV + k);
-}
-
-// y = H x.  Bond masks and coefficients J_b/2 are staged in shared memory
-// from the handle's bond table [J (nb) | masks (nb) | sum J / 4].
+// y = H x (the row loop of xd_u1_rows.cuh).
 template <typename T, int NV>
 __global__ void __launch_bounds__(kThreads) k_apply(U1View u, const double *__restrict__ bond,
                                                     int nb, const T *__restrict__ x,
@@ -87,43 +32,10 @@ __global__ void __launch_bounds__(kThreads) k_apply(U1View u, const double *__re
     uint64_t *sm_mask = (uint64_t *)smem;
     T *sm_half = (T *)(sm_mask + nb);
     __shared__ uint64_t sh_range[2];
-    const uint64_t *masks = (const uint64_t *)(bond + nb);
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        sm_half[b] = (T)(0.5 * bond[b]);
-        sm_mask[b] = masks[b];
-    }
+    stage_bonds(bond, nb, sm_mask, sm_half);
     const T jq = (T)bond[2 * nb];
     __syncthreads();
-
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < u.dim;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = base + threadIdx.x;
-        RowState rs = unrank_tile(u, base, r, sh_range);
-        if (!rs.valid) continue;
-        const uint64_t s = rs.s;
-        T acc[NV];
-#pragma unroll
-        for (int k = 0; k < NV; ++k) acc[k] = T(0);
-        T dsub = T(0);
-        for (int b = 0; b < nb; ++b) {
-            const uint64_t mk = sm_mask[b];
-            const uint64_t t = s & mk;
-            if (t != 0 && t != mk) {
-                const int64_t c = rank_of(u, s ^ mk);
-                const T cf = sm_half[b];
-                T xv[NV];
-                load_row<T, NV>(x, c, xv);
-#pragma unroll
-                for (int k = 0; k < NV; ++k) acc[k] += cf * xv[k];
-                dsub += cf;
-            }
-        }
-        T xr[NV];
-        load_row<T, NV>(x, r, xr);
-        const T d = jq - dsub;
-#pragma unroll
-        for (int k = 0; k < NV; ++k) y[r * NV + k] = d * xr[k] + acc[k];
-    }
+    apply_rows<T, NV, false>(u, sm_mask, sm_half, nb, jq, x, y, sh_range);
 }
 
 // State words of rows [first, first + count): the block of row r is the last
