@@ -57,6 +57,27 @@ def test_ground_state_vector_and_residual(orc):
     assert info["resid"][0] < 1e-6
 
 
+@pytest.mark.parametrize("storage", [torch.float64, torch.float32])
+def test_ground_state_two_passes_agree_on_small_blocks(orc, storage):
+    """Small U(1) blocks run the first Lanczos pass in one cooperative launch
+    and the second pass (the eigenvector from the recorded alpha and beta) as
+    separate products; the second pass must rebuild the first pass's vectors,
+    so after 250 steps (far past convergence, where a mismatch grows) the
+    vector is still the ground state, in both storage types."""
+    A = api()
+    N = 14
+    bonds, J = W.chain_j1j2(N, 1.0, 0.3)  # a single ground state (J2 = 1/2 has two)
+    st = orc.enumerate_states(N, 7)
+    w, V = np.linalg.eigh(orc.dense_u1(N, st, bonds, J))
+    assert w[1] - w[0] > 1e-3
+    ham = A.Hamiltonian(A.Basis(N, 7, bonds), J)
+    e0, psi, info = ham.ground_state(max_iter=250, seed=5, storage=storage)
+    tol = 1e-10 if storage == torch.float64 else 1e-6
+    assert abs(e0 - w[0]) <= tol * abs(w[0])
+    p = psi.double().cpu().numpy()
+    assert abs(abs(p @ V[:, 0]) / np.linalg.norm(p) - 1) < (1e-8 if storage == torch.float64 else 1e-4)
+
+
 def test_bilinear_matches_oracle(orc):
     A = api()
     # bond counts cover one to eight bonds per warp and two launches of 256
