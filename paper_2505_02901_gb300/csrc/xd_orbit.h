@@ -113,9 +113,9 @@ XD_HD bool torus_narrow(const TorusGeo &g, uint64_t w, uint32_t top, uint64_t &M
     uint64_t img = (uint64_t)top << (g.Lx * ytop);
     bool tight = bounded && torus_row(g, bound, ytop) == top;  // image prefix == bound prefix
     for (int y = ytop - 1; y >= 0; --y) {
-        if ((M & (M - 1)) == 0) {  // one candidate: its image in one go
+        if ((M & (M - 1)) == 0) {  // one candidate: its image in one go (the identity: w)
             const int q = orb_ctz(M);
-            *img_out = torus_translate(g, w, q & 7, q >> 3);
+            *img_out = q ? torus_translate(g, w, q & 7, q >> 3) : w;
             return !(tight && *img_out > bound);
         }
         uint32_t vmin = 0xffffffffu;
