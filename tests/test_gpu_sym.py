@@ -31,8 +31,12 @@ def _space_group(L):
     return L * L, b, J, g, np.ones(len(g), dtype=np.complex128)
 
 
+# tori: rows of up to 7 sites take the row-state search with its row-step
+# table; 8 sites (8x2) the narrowing from the word; more than 8 rows (2x9)
+# the scan over the translations reaching the smallest top row
 CASES = [_chain(8, 0), _chain(8, 4), _chain(10, 1), _chain(12, 3), _chain(13, 2),
          _torus(3, 3, 1, 0), _torus(4, 4, 0, 0), _torus(4, 4, 1, 2), _torus(2, 6, 1, 1),
+         _torus(8, 2, 1, 1), _torus(8, 2, 0, 0), _torus(2, 9, 1, 3),
          _dihedral(8, 0, 1), _dihedral(10, 5, -1), _dihedral(12, 0, -1), _dihedral(12, 6, 1),
          _space_group(4)]
 
