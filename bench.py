@@ -576,11 +576,22 @@ def run_space_group(lattice: str, nup: int):
 
 def run_profile_case(case: str):
     """apply8: Y = H X with eight FP32 columns on the benchmark lattice;
-    bilinear: per-bond forms <g|S_i.S_j|x> of the 56-bond ladder in FP64."""
+    bilinear: per-bond forms <g|S_i.S_j|x> of the 56-bond ladder in FP64;
+    batch: the batched product of 64 uneven instances (one fused launch)."""
     import torch
 
     from paper_2505_02901_gb300 import api, build, workloads as W
     build.build()
+    if case == "batch":
+        insts = W.batched_instances(64, seed=4)
+        hams = [api.Hamiltonian(api.Basis(d["N"], d["nup"], d["bonds"]), d["J"]) for d in insts]
+        xs = [torch.stack([api.random_vector(h.dim, 1000 * k + v, torch.float64) for v in range(8)], 1)
+              .float().contiguous() for k, h in enumerate(hams)]
+        ys = [torch.empty_like(x) for x in xs]
+        ms = _event_time(lambda: api.batch_apply(hams, xs, ys), reps=3)
+        print(json.dumps({"case": case, "workload": "64 chains and ladders, N 18-28, 8 FP32 vectors each",
+                          "rows": sum(h.dim for h in hams), "ms": ms}))
+        return 0
     if case == "apply8":
         bonds, J = W.square_j1j2(LX, LY, J1, J2)
         h = api.Hamiltonian(api.Basis(N, NUP, bonds), J)
@@ -611,7 +622,7 @@ def main():
     ap.add_argument("--only", action="store_true", help="time the headline form only")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-row measurements")
     ap.add_argument("--case", default="bench",
-                    choices=["bench", "sym-chain", "space-group", "apply8", "bilinear"],
+                    choices=["bench", "sym-chain", "space-group", "apply8", "bilinear", "batch"],
                     help="single products for profiling captures, four launches each: sym-chain, "
                          "the symmetric product of the N-site chain with its translations and "
                          "reflections (fully symmetric irrep, N from --chain-n); space-group, the "
@@ -619,7 +630,8 @@ def main():
                          "(--group square or triangular) or its translations (--group translations), "
                          "--nup; apply8, the "
                          "eight-vector FP32 product on the --lattice block; bilinear, the per-bond "
-                         "forms of the 56-bond ladder (FP64)")
+                         "forms of the 56-bond ladder (FP64); batch, the batched product of 64 "
+                         "chains and ladders with eight FP32 vectors each")
     ap.add_argument("--chain-n", type=int, default=32)
     ap.add_argument("--group", default="square", choices=["square", "triangular", "translations"])
     ap.add_argument("--nup", type=int, default=18)
@@ -639,7 +651,7 @@ def main():
         return run_sym_chain(args.chain_n)
     if args.case == "space-group":
         return run_space_group(args.group, args.nup)
-    if args.case in ("apply8", "bilinear"):
+    if args.case in ("apply8", "bilinear", "batch"):
         return run_profile_case(args.case)
 
     import numpy as np
