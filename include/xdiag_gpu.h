@@ -277,11 +277,18 @@ xd_status xd_random_vector(int64_t dim, uint64_t seed, void *out,
 
 /* ys[k] = H_k xs[k] for ninst independent U(1) Hamiltonians of uneven size
  * in one persistent launch (the multi-vector apply of Sec. 5.1 over many
- * blocks).  xs, ys: host arrays of ninst device pointers, each [dim_k][nvec];
- * dtype XD_F32 or XD_F64; nvec in {1, 2, 4, 8}.  The tile schedule is chosen
- * by the library's autotuner on first use of a (set, dtype, nvec) and the
- * launch is replayed from a captured CUDA graph while the pointers are
- * unchanged.  Asynchronous. */
+ * blocks).  xs, ys: host arrays of ninst device pointers, each [dim_k][nvec]
+ * (16-byte aligned for the eight-vector block product), x != y; dtype
+ * XD_F32 or XD_F64; nvec in {1, 2, 4, 8}.  With eight FP32 right-hand sides
+ * the operators large enough for the prefix-block layout (N >= 24, up to
+ * 96 of them) are done inside the same launch by the eight-vector block
+ * product.  The tile schedule is chosen by the library's autotuner (median
+ * of five timings per candidate) on first use of a (set, dtype, nvec, stream)
+ * and the launch is replayed from a captured CUDA graph while the pointers
+ * are unchanged; new couplings of a member (xd_ham_set_couplings) or its
+ * destruction drop the captured launch.  Errors: XD_EINVAL (NULL arrays or
+ * vectors, x == y, a symmetric block, dtype or nvec), XD_ERANGE (more than
+ * 512 bonds in an instance).  Asynchronous. */
 xd_status xd_batch_apply(int ninst, const xd_ham *hs, const void *const *xs,
                          void *const *ys, xd_dtype dtype, int nvec,
                          xd_stream stream);
