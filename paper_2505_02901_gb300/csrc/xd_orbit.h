@@ -219,6 +219,68 @@ XD_HD uint64_t torus_top_rows(const TorusGeo &g, uint64_t PM, uint64_t PA, uint3
     return ((Mr << 8) | (Mr >> sh)) & (~0ull >> (64 - 8 * g.Ly));
 }
 
+// Top step from the three smallest rows of the word (translations alone,
+// rows of at most 7 sites).  For a word w, RowTop3 holds the three smallest
+// row minima in ascending order (ties kept) with their rows, and for each
+// such value the candidates of every row reaching it (bits a + 8 b, b the
+// translation bringing the row to the top).  A flip that changes rows y1
+// and y2 leaves the others as they were: the smallest of those is the first
+// of the three whose row is neither y1 nor y2, and its candidates are those
+// of its value with rows y1 and y2 taken out; the two new rows join from the
+// row table.  torus_top_flip then gives what torus_top gives on the flipped
+// word.
+struct RowTop3 {
+    uint32_t v;   // bytes 0..2: the three smallest minima (0xff: fewer rows)
+    uint32_t y;   // bytes 0..2: their rows
+    uint64_t m0, m1, m2;
+};
+
+XD_HD uint64_t row_cands(const TorusGeo &g, int y, uint32_t am) {
+    return (uint64_t)am << (y + 1 == g.Ly ? 0 : 8 * (y + 1));
+}
+
+XD_HD void torus_top3(const TorusGeo &g, uint64_t w, RowTop3 &t) {
+    uint32_t v0 = 0xffu, v1 = 0xffu, v2 = 0xffu, y0 = 0, y1 = 0, y2 = 0;
+    for (int y = 0; y < g.Ly; ++y) {  // insertion into the three smallest (stable)
+        const uint32_t val = g.rowtab[torus_row(g, w, y)] & 0xffu;
+        if (val < v0) {
+            v2 = v1; y2 = y1; v1 = v0; y1 = y0; v0 = val; y0 = (uint32_t)y;
+        } else if (val < v1) {
+            v2 = v1; y2 = y1; v1 = val; y1 = (uint32_t)y;
+        } else if (val < v2) {
+            v2 = val; y2 = (uint32_t)y;
+        }
+    }
+    t.v = v0 | (v1 << 8) | (v2 << 16);
+    t.y = y0 | (y1 << 8) | (y2 << 16);
+    t.m0 = t.m1 = t.m2 = 0;
+    for (int y = 0; y < g.Ly; ++y) {
+        const uint32_t e = g.rowtab[torus_row(g, w, y)], val = e & 0xffu;
+        const uint64_t c = row_cands(g, y, e >> 8);
+        if (val == v0) t.m0 |= c;
+        if (val == v1) t.m1 |= c;
+        if (val == v2) t.m2 |= c;
+    }
+}
+
+XD_HD uint64_t torus_top_flip(const TorusGeo &g, const RowTop3 &t, uint64_t w, int y1, int y2, uint32_t *top) {
+    // the smallest row left untouched: the first of the three that is neither y1 nor y2
+    const int r0 = (int)(t.y & 0xffu), r1 = (int)((t.y >> 8) & 0xffu);
+    const bool k0 = r0 != y1 && r0 != y2, k1 = r1 != y1 && r1 != y2;
+    const uint32_t ex = k0 ? (t.v & 0xffu) : k1 ? ((t.v >> 8) & 0xffu) : ((t.v >> 16) & 0xffu);
+    const uint64_t mx = k0 ? t.m0 : k1 ? t.m1 : t.m2;
+    const uint64_t keep = ~row_cands(g, y1, 0xffu) & ~row_cands(g, y2, 0xffu);
+    const uint32_t e1 = g.rowtab[torus_row(g, w, y1)], e2 = g.rowtab[torus_row(g, w, y2)];
+    const uint32_t v1 = e1 & 0xffu, v2 = e2 & 0xffu;
+    uint32_t best = ex < v1 ? ex : v1;
+    best = best < v2 ? best : v2;
+    uint64_t M = ex == best ? (mx & keep) : 0;
+    if (v1 == best) M |= row_cands(g, y1, e1 >> 8);
+    if (v2 == best) M |= row_cands(g, y2, e2 >> 8);
+    *top = best;
+    return M;
+}
+
 struct TorusOrbit {
     uint64_t rep;  // smallest image
     int k, q;      // a winning coset and translation (bit q = a + 8 b)

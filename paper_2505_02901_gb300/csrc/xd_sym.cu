@@ -497,8 +497,10 @@ __global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, SymBonds sbo,
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < v.dim;
          r += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t s = __ldg(v.reps + r);
-        uint64_t PM = 0, PA = 0;  // row state of s
-        if (rows) torus_rows(tgeo, s, PM, PA);
+        uint64_t PM = 0, PA = 0;  // row state of s (cosets)
+        RowTop3 t3;               // its three smallest rows (translations alone)
+        if (rows && !COS) torus_top3(tgeo, s, t3);
+        else if (rows) torus_rows(tgeo, s, PM, PA);
         if constexpr (COS) {
             for (int k = 1; k < v.tnp; ++k) {
                 const uint64_t w = act(v.act, v.nchunk, __ldg(v.tpp + k), s);
@@ -536,9 +538,16 @@ __global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, SymBonds sbo,
                     const int b = sm_perm[bs];  // bond id (point-image and row tables)
                     Orbit o;
                     if (rows) {
-                        // p_k of the flipped word, its row state refreshed in the two rows of the flip
+                        // p_k of the flipped word and its top step: from the three smallest
+                        // rows of s (translations alone), or from the row state of p_k s
+                        // refreshed in the two rows of the flip (cosets)
                         o = torus_result(v, torus_orbit_top(tgeo, COS ? v.tnp : 1,
                                                             [&](int k, uint64_t *w, uint32_t *top) {
+                            if (!COS) {
+                                *w = s ^ mk;
+                                const uint32_t rr = sm_krow[b];
+                                return torus_top_flip(tgeo, t3, *w, rr & 0xffu, rr >> 8, top);
+                            }
                             uint64_t pm = PM, pa = PA;
                             if (COS && k) {
                                 const int e = (k - 1) * kThreads + threadIdx.x;

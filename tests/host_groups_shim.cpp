@@ -84,3 +84,28 @@ extern "C" int64_t shim_top_rows_mismatch(int N, int G, const int32_t *perms, co
     }
     return bad;
 }
+
+// The top step from the three smallest rows (xd_orbit.h) against the top
+// step of s ^ (bit i | bit j) from the word; number of differing words.
+extern "C" int64_t shim_top3_mismatch(int N, int G, const int32_t *perms, const int32_t *bonds, int nb, int64_t n,
+                                      const uint64_t *s, const int32_t *ij) {
+    xd::GroupTables T;
+    xd::group_tables(N, G, perms, bonds, nb, &T);
+    if (!T.tx || T.ty > 8) return -1;
+    if (T.tx > 7) return -2;
+    std::vector<uint16_t> rowtab(1u << T.tx);
+    for (size_t r = 0; r < rowtab.size(); ++r) rowtab[r] = (uint16_t)(T.minrot[r] | (T.amask[r] << 8));
+    const xd::TorusGeo g = xd::torus_geo(T.tx, T.ty, rowtab.data());
+    int64_t bad = 0;
+    for (int64_t q = 0; q < n; ++q) {
+        xd::RowTop3 t;
+        xd::torus_top3(g, s[q], t);
+        const int i = ij[2 * q], j = ij[2 * q + 1];
+        const uint64_t w = s[q] ^ (1ull << i) ^ (1ull << j);
+        uint32_t t1, t2;
+        const uint64_t M1 = xd::torus_top_flip(g, t, w, i / T.tx, j / T.tx, &t1);
+        const uint64_t M2 = xd::torus_top(g, w, &t2);
+        bad += (t1 != t2 || M1 != M2);
+    }
+    return bad;
+}

@@ -303,3 +303,30 @@ def test_torus_incremental_top_step(shim, case):
         assert bad == -2  # rows of 8 sites take the search from the word
         return
     assert bad == 0, name
+
+
+@pytest.mark.parametrize("case", range(len(TORUS_CASES)))
+def test_torus_top_step_from_three_smallest_rows(shim, case):
+    """The top step of a flipped word from the three smallest rows of the
+    word before the flip (the rows it leaves untouched) and the two new rows
+    equals the top step computed from the flipped word: random words, zero
+    and full words, random site pairs (same row and different rows)."""
+    name, perms, bonds, nup = TORUS_CASES[case]
+    perms = np.ascontiguousarray(perms, dtype=np.int32)
+    bonds = np.ascontiguousarray(bonds, dtype=np.int32)
+    G, N = perms.shape
+    rng = np.random.default_rng(13 + case)
+    n = 20000
+    words = np.array([sum(1 << int(i) for i in rng.choice(N, size=int(rng.integers(0, N + 1)), replace=False))
+                      for _ in range(n)] + [0, (1 << N) - 1], dtype=np.uint64)
+    ij = np.ascontiguousarray(np.stack([rng.choice(N, 2, replace=False) for _ in range(len(words))]), dtype=np.int32)
+    P = ctypes.POINTER
+    shim.shim_top3_mismatch.restype = ctypes.c_int64
+    shim.shim_top3_mismatch.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_int32),
+                                        ctypes.c_int, ctypes.c_int64, P(ctypes.c_uint64), P(ctypes.c_int32)]
+    bad = shim.shim_top3_mismatch(N, G, _p(perms, ctypes.c_int32), _p(bonds, ctypes.c_int32), len(bonds),
+                                  len(words), _p(words, ctypes.c_uint64), _p(ij, ctypes.c_int32))
+    if name.startswith("8x8"):
+        assert bad == -2
+        return
+    assert bad == 0, name
