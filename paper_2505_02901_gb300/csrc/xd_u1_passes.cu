@@ -269,6 +269,7 @@ __global__ void __launch_bounds__(kT, 2) k_tpass(TPassParams p, const typename P
     using C = typename Pol::C;
     using Acc = typename Pol::Acc;
     using R = Rows<V, kTQ>;
+    using RA = Rows<Acc, kTQ>;  // the accumulator tile, rotated like the x tile
     constexpr int K = kK;
     if (Pol::kMode >= 0 && __ldg(p.state + 1) != Pol::kMode) return;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(kT, 2) k_tpass(TPassParams p, const typename P
             const int r = e / kTQ, j = e % kTQ;
             if (j < nq) {
                 cp_async_n(tile + R::at(r, j), x + bo[r] + j, (int)sizeof(V));
-                if (!FIRST) cp_async_n(atile + e, acc + bo[r] + j, (int)sizeof(Acc));
+                if (!FIRST) cp_async_n(atile + RA::at(r, j), acc + bo[r] + j, (int)sizeof(Acc));
             } else {
                 tile[R::at(r, j)] = Pol::zero_v();
             }
@@ -339,10 +340,12 @@ __global__ void __launch_bounds__(kT, 2) k_tpass(TPassParams p, const typename P
                     }
                 }
                 const int64_t base = bo[r];
+                Acc prev[kTQ];
+                if (!FIRST) RA::load(atile, r, prev);  // 16-byte reads of the rotated row
 #pragma unroll
                 for (int j = 0; j < kTQ; ++j)
                     if (j < nq) {
-                        if (!FIRST) Pol::merge(a[j], atile[r * kTQ + j]);
+                        if (!FIRST) Pol::merge(a[j], prev[j]);
                         acc[base + j] = a[j];
                     }
             }
