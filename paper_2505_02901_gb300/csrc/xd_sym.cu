@@ -497,9 +497,12 @@ __global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, SymBonds sbo,
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < v.dim;
          r += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t s = __ldg(v.reps + r);
-        uint64_t PM = 0, PA = 0;  // row state of s (cosets)
-        RowTop3 t3;               // its three smallest rows (translations alone)
-        if (rows && !COS) torus_top3(tgeo, s, t3);
+        // translations alone, real blocks: the three smallest rows of s; otherwise
+        // the row state of s (the complex form keeps its registers below 64 so)
+        constexpr bool kTop3 = !COS && !CPLX;
+        uint64_t PM = 0, PA = 0;
+        RowTop3 t3;
+        if (rows && kTop3) torus_top3(tgeo, s, t3);
         else if (rows) torus_rows(tgeo, s, PM, PA);
         if constexpr (COS) {
             for (int k = 1; k < v.tnp; ++k) {
@@ -539,11 +542,11 @@ __global__ void __launch_bounds__(kThreads) k_sym_apply(SymView v, SymBonds sbo,
                     Orbit o;
                     if (rows) {
                         // p_k of the flipped word and its top step: from the three smallest
-                        // rows of s (translations alone), or from the row state of p_k s
-                        // refreshed in the two rows of the flip (cosets)
+                        // rows of s (kTop3), or from the row state of p_k s refreshed in the
+                        // two rows of the flip
                         o = torus_result(v, torus_orbit_top(tgeo, COS ? v.tnp : 1,
                                                             [&](int k, uint64_t *w, uint32_t *top) {
-                            if (!COS) {
+                            if (kTop3) {
                                 *w = s ^ mk;
                                 const uint32_t rr = sm_krow[b];
                                 return torus_top_flip(tgeo, t3, *w, rr & 0xffu, rr >> 8, top);
