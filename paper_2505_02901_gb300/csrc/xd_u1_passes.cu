@@ -137,6 +137,7 @@ struct MainParams;
 
 struct PolDF {
     static constexpr int kMode = 0;
+    static constexpr bool kFoldCross = false;  // a cross flip adds c (x_target - x_row) in pairs
     using V = float2;     // scaled x as (hi, lo)
     using C = float2;     // flip coefficient J/2 as (C, gamma)
     using D = float2;     // diagonal as (C, gamma)
@@ -168,6 +169,9 @@ struct PolDF {
 
 struct PolFX {
     static constexpr int kMode = 1;
+    // a cross flip adds c x_target, and its -c x_row joins the row's integer
+    // diagonal (exact: the same integers summed in another order)
+    static constexpr bool kFoldCross = true;
     using V = long long;  // round(2^S x)
     using C = int;        // 2 k_b, in units of q/4
     using D = int;        // D(s) = sum_b k_b eps_b, in units of q/4
@@ -534,10 +538,14 @@ __global__ void __launch_bounds__(kT, 2) k_main(MainParams p, const typename Pol
         __syncthreads();
 
         Acc acc[K][KB];
+        C cs[K][KB];  // kFoldCross: the row's sum of the cross flips' coefficients
 #pragma unroll
         for (int r = 0; r < K; ++r)
 #pragma unroll
-            for (int k = 0; k < KB; ++k) Pol::zero(acc[r][k]);
+            for (int k = 0; k < KB; ++k) {
+                Pol::zero(acc[r][k]);
+                cs[r][k] = C();
+            }
         uint32_t lw[K];
 #pragma unroll
         for (int r = 0; r < K; ++r) lw[r] = __ldg(p.lo_list + l0 + min(tid + r * kT, n - 1));
@@ -601,7 +609,7 @@ __global__ void __launch_bounds__(kT, 2) k_main(MainParams p, const typename Pol
                 if (i < n) {
                     const uint32_t l = lw[r];
                     V xv[KB];
-                    R::load(xs, i, xv);
+                    if (!Pol::kFoldCross) R::load(xs, i, xv);
 #pragma unroll 1
                     for (int q = q0; q < q1; ++q) {
                         const uint32_t meta = cmeta[q];
@@ -613,7 +621,14 @@ __global__ void __launch_bounds__(kT, 2) k_main(MainParams p, const typename Pol
                             R::load(nb, (int)r2, nv);
 #pragma unroll
                             for (int k = 0; k < KB; ++k)
-                                if ((fm >> k) & 1u) Pol::add_diff(acc[r][k], cq, nv[k], xv[k]);
+                                if ((fm >> k) & 1u) {
+                                    if constexpr (Pol::kFoldCross) {
+                                        Pol::add(acc[r][k], cq, nv[k]);
+                                        cs[r][k] += cq;
+                                    } else {
+                                        Pol::add_diff(acc[r][k], cq, nv[k], xv[k]);
+                                    }
+                                }
                         }
                     }
                 }
@@ -633,7 +648,9 @@ __global__ void __launch_bounds__(kT, 2) k_main(MainParams p, const typename Pol
                     if (hk[k] != kEmpty) {
                         Acc a = acc[r][k];
                         Pol::merge(a, acc_in[sh_off[k] + i]);
-                        y[sh_off[k] + i] = Pol::result(a, sh_dpre[k], dp, xv[k], oset);
+                        D dk = sh_dpre[k];
+                        if constexpr (Pol::kFoldCross) dk -= cs[r][k];
+                        y[sh_off[k] + i] = Pol::result(a, dk, dp, xv[k], oset);
                     }
             }
         }
