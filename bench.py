@@ -48,7 +48,7 @@ FORM_NOTE = {
 # FP64: the sum over the product's kernels, captured at 4x7 (the 4x8 workload
 # holds too much device memory for a multi-pass capture) and scaled to 4x8
 # by rows (profiles/apply64_4x7_passes_full.md)
-TRAFFIC = {"f32": 71.64e9, "f64": 3.4215e9 * 601080390 / 40116600}
+TRAFFIC = {"f32": 71.64e9, "f64": 3.4073e9 * 601080390 / 40116600}
 # the kernels each form's product runs at this workload
 KERNEL = {"f32": "k_spmm<12>",
           "f64": "k_x64_stats, k_x64_convert, 2 x k_tpass<PolFX>, k_main<PolFX, 4> (dominant, 56%)"}
